@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the fused PQQA replica-update path on GB300.
+
+One bench step = one whole anneal of the workload's batch of instances: the
+initial draw, all K annealing steps (one fused kernel per step, replayed from
+CUDA graphs in chunks of `round_every` steps), the periodic projection
+rounding with exact costs after every chunk, and the final evaluation.
+
+Default workload (N = 1): MIS on 16 Erdos-Renyi graphs with n uniform in
+[700, 800] and p = 0.15, S = 128 replicas, 3000 steps, FP32 state (the shape of
+the paper's ER-[700-800] benchmark, Sec. 5.1 and Table 7). Under torchrun each
+rank anneals its own 16 graphs (weak scaling, no data-path collective).
+
+Printed: one JSON line with replica-steps/s over all ranks, the end-to-end
+figure through the host-buffer API, the roofline of the fused step kernel,
+the FP64 CPU oracle on a bounded sample, and the clocks seen while timing.
+`--impl reference` times the oracle itself on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from qqa_inputs import workloads as W  # noqa: E402
+
+METRIC = "replica-steps/s"
+BYTES_PER_ELEMENT_STEP = {W.FP32: 24, W.BF16: 20}   # compulsory HBM bytes of one (node, replica) update
+
+
+def build_workload(name: str, rank: int):
+    if name == "mis_er700_800":
+        return W.er_mis_paper(num_graphs=16, S=128, steps=3000, base_seed=1000 + 16 * rank)
+    if name == "mis_er100":
+        return W.er_mis_small(seed=rank)
+    if name == "maxcut_regular3":
+        return W.maxcut_large(family="regular3", seed=7 + rank)
+    if name == "maxcut_ba4":
+        return W.maxcut_large(family="ba4", seed=7 + rank)
+    if name == "mis_cliqueblocks512":
+        return W.batched_mis(base_seed=5000 + 512 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes_per_launch(wl) -> int:
+    total = 0
+    for inst in wl.instances:
+        g, p = inst.graph, inst.params
+        total += g.n * p.S * BYTES_PER_ELEMENT_STEP[p.precision] + 4 * g.nnz + 4 * (g.n + 1)
+        if g.w is not None:
+            total += 4 * g.nnz
+    return total
+
+
+def read_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_02135_gb300", "csrc")
+    for name in ("step_impl.cuh", "qqa_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.out = os.path.join("/tmp", f"qqa_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.out):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- oracle leg
+def oracle_sample(wl, budget_steps: int):
+    """The FP64 oracle on a bounded sample: the first instance, the first
+    `budget_steps` steps of its schedule. Returns (replica-steps/s, seconds, cores, description)."""
+    import oracle
+    inst = wl.instances[0]
+    steps = min(budget_steps, inst.params.steps)
+    t0 = time.perf_counter()
+    oracle.anneal(inst.kind, inst.graph, inst.params, steps=steps)
+    dt = time.perf_counter() - t0
+    desc = (f"1 of {len(wl.instances)} instances ({inst.name}, n={inst.graph.n}, S={inst.params.S}), "
+            f"first {steps} of {inst.params.steps} steps, FP64")
+    return inst.params.S * steps / dt, dt, oracle.num_threads(), desc
+
+
+def oracle_steps_for(wl, seconds: float) -> int:
+    inst = wl.instances[0]
+    import oracle
+    probe = min(20, inst.params.steps)
+    t0 = time.perf_counter()
+    oracle.anneal(inst.kind, inst.graph, inst.params, steps=probe)
+    per = (time.perf_counter() - t0) / probe
+    return max(1, min(inst.params.steps, int(seconds / max(per, 1e-9))))
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    wl = build_workload(args.workload, 0)
+    steps = oracle_steps_for(wl, args.ref_seconds)
+    for _ in range(args.warmup):
+        oracle_sample(wl, steps)
+    vals, secs = [], []
+    cores, desc = None, None
+    for _ in range(args.steps):
+        v, dt, cores, desc = oracle_sample(wl, steps)
+        vals.append(v)
+        secs.append(dt)
+    value = len(vals) * wl.instances[0].params.S * steps / sum(secs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- our leg
+def run_ours(args):
+    import torch
+    import paper_2409_02135_gb300 as qqa
+    from paper_2409_02135_gb300 import _build
+
+    world, rank, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    _build.build()
+    wl = build_workload(args.workload, rank)
+    stream = torch.cuda.current_stream()
+    alloc = qqa.torch_allocator()
+    kinds = [inst.kind for inst in wl.instances]
+    probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
+    params = [qqa.make_params(inst.params) for inst in wl.instances]
+    cfg = qqa.LaunchConfig(use_graphs=1)
+    run = qqa.Run.create(probs, params, config=cfg, stream=stream, allocator=alloc)
+    K = max(p.steps for p in params)
+    R = min(p.round_every for p in params) or K
+    chunks = (K + R - 1) // R
+    replica_steps = sum(p.S * p.steps for p in params)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > 129 MB L2
+
+    def one_anneal(seed, chunk_events=None):
+        run.reset(seed)
+        for c in range(chunks):
+            if chunk_events is not None:
+                chunk_events[c][0].record(stream)
+            run.steps(min(R, K - c * R))
+            if chunk_events is not None:
+                chunk_events[c][1].record(stream)
+            run.eval()
+
+    for w in range(args.warmup):
+        one_anneal(10_000 + w)
+    torch.cuda.synchronize()
+
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    chunk_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(chunks)]
+                for _ in range(args.steps)]
+    launches0 = qqa.launch_count()
+    with ClockSampler(local) as clocks:
+        barrier(world)
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                         # evict L2 between timed anneals
+            step_ev[k][0].record(stream)
+            one_anneal(20_000 + k, chunk_ev[k])
+            step_ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - wall0
+    launches = qqa.launch_count() - launches0
+    run.sync()
+    ms = [a.elapsed_time(b) for a, b in step_ev]
+    dev_s = sum(ms) / 1000.0
+    dev_s_max = max_over_ranks(dev_s, world)
+    total_rs = sum_over_ranks(replica_steps * args.steps, world)
+    value = total_rs / dev_s_max
+
+    # fused step kernel: average launch duration from the chunk events
+    step_ms = sum(a.elapsed_time(b) for ev in chunk_ev for a, b in ev)
+    step_launches = args.steps * K
+    avg_launch_s = step_ms / 1000.0 / step_launches
+    alg_bytes = algorithmic_bytes_per_launch(wl)
+    peak, peak_kind = read_peak()
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(args.workload), "peak_source": peak_kind,
+                "kernel": "qqa_step_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "avg_launch_us": avg_launch_s * 1e6, "step_share_of_device_time": step_ms / sum(ms)}
+
+    # end to end through the public API with host buffers (CSR in, results out)
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        h2d = sum(4 * (i.graph.n + 1) + 4 * i.graph.nnz + (4 * i.graph.nnz if i.graph.w is not None else 0)
+                  for i in wl.instances)
+        d2h = sum(p.S * (8 + 8 + 1 + 8) + 4 + 4 * ((i.graph.n + 31) // 32) for p, i in zip(params, wl.instances))
+        times = []
+        for k in range(args.e2e_steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eprobs = [qqa.Problem(i.kind, i.graph, stream=stream, allocator=alloc) for i in wl.instances]
+            eparams = [qqa.make_params(i.params, seed=30_000 + k) for i in wl.instances]
+            erun = qqa.anneal(eprobs, eparams, config=cfg, stream=stream, allocator=alloc)
+            out = [erun.result(j) for j in range(len(eprobs))]
+            erun.close()
+            for pb in eprobs:
+                pb.close()
+            dt = time.perf_counter() - t0
+            if k > 0:                     # the first call also builds the CUDA graphs
+                times.append(dt)
+            assert all(o["best"] >= -1 for o in out)
+        e2e_s = max_over_ranks(sum(times), world)
+        e2e = {"value": sum_over_ranks(replica_steps * len(times), world) / e2e_s, "unit": METRIC,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(times)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        steps = oracle_steps_for(wl, args.cpu_seconds)
+        v, dt, cores, desc = oracle_sample(wl, steps)
+        cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    quality = []
+    for j in range(len(probs)):
+        r = run.result(j, with_x=False)
+        quality.append(int(r["obj"][r["best"]]) if r["best"] >= 0 else None)
+
+    prec = wl.instances[0].params.precision
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == W.FP32 else "bf16-storage/f32-math", "data": "synthetic",
+        "config": {"workload": wl.name, "instances": len(wl.instances), "replicas": wl.instances[0].params.S,
+                   "anneal_steps": K, "round_every": R, "precision": "fp32" if prec == W.FP32 else "bf16",
+                   "l2": "flushed between timed anneals (512 MB write)",
+                   "parallelism": f"instances x{world} ranks" if world > 1 else "single GPU",
+                   "launch": {"group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
+                              "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
+                              "graphs": True}},
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+        "gpu_launches": launches, "clocks": clocks.summary(),
+        "replica_node_updates_per_s": sum_over_ranks(sum(i.graph.n * i.params.S * i.params.steps
+                                                         for i in wl.instances) * args.steps, world) / dev_s_max,
+        "wall_s_timed_region": wall, "best_objective_per_instance": quality,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mis_er700_800",
+                    choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * qqa.h -- C ABI of libqqa, the GB300 (sm_103a) implementation of the
+ * per-step replica update of Parallel Quasi-Quantum Annealing (PQQA;
+ * Ichikawa & Arai, arXiv 2409.02135).
+ *
+ * What one annealing step computes, for every node i and replica s of every
+ * instance (Sec. 3.2-3.4, Sec. 5 "Implementation", App. C.2-C.3, App. D.1):
+ *   g   = d l^/dp  (MIS Eq. 22, max-clique Eq. 24, max-cut Eq. 26; A p by CSR SpMM)
+ *       + gamma_t * d s/dp           alpha-entropy, Eq. 7; gamma_t linear (App. C.2)
+ *       - alpha (p - mean_i)/STD_i   communication term of Eq. 10
+ *   p  <- AdamW(p, g) + sqrt(2 lr T) xi,  then clamp to [0, 1]   (Eq. 11, Sec. 3.4)
+ * and every `round_every` steps (and at the end) the projection rounding
+ * x = [p > 1/2] with the exact integer cost and feasibility of every replica
+ * (Sec. 5 "Implementation").
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: QQA_OK (0) or a negative QQA_E* code; qqa_last_error()
+ *     then holds a message for the calling thread.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *     stream-ordered; entry points that return host data synchronise it.
+ *   - Host arrays passed in are copied; the caller keeps ownership. Host
+ *     output arrays are allocated by the caller. Device memory is owned by
+ *     the library and comes from `alloc` when given, else cudaMalloc.
+ *   - Replica state is node-major: element (i, s) at i*S + s.
+ *   - Objective convention: maximisation units (independent-set size, cut
+ *     weight, clique size). `energy` is the penalised minimisation energy
+ *     l(x) of Eq. 2 with penalty lambda.
+ *   - Nothing here falls back to the CPU: without a usable CUDA device every
+ *     call that touches the GPU returns QQA_ECUDA.
+ */
+#ifndef QQA_H
+#define QQA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QQA_OK 0
+#define QQA_EINVAL (-1)     /* bad argument or malformed graph */
+#define QQA_ENOMEM (-2)     /* device or host allocation failed, or over budget */
+#define QQA_ECUDA (-3)      /* a CUDA call failed (message in qqa_last_error) */
+#define QQA_ETIMEOUT (-4)   /* a bounded device wait ran out */
+#define QQA_ENONFINITE (-5) /* a non-finite gradient or state value was produced */
+#define QQA_EBUSY (-6)      /* no free slot / request not finished */
+
+typedef enum { QQA_MIS = 0, QQA_MAXCUT = 1, QQA_MAXCLIQUE = 2 } qqa_kind;
+typedef enum { QQA_FP32 = 0, QQA_BF16 = 1 } qqa_precision;
+
+/* Optional device allocator (e.g. a framework's caching allocator). */
+typedef struct qqa_allocator {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} qqa_allocator;
+
+/*
+ * Hyper-parameters of one instance. Paper values (Sec. 5, App. C.2, C.3,
+ * App. D.1): a_ent = 4, gamma_min = -2 (max-cut: -5, or -20 on large graphs),
+ * gamma_max = 0.1, weight_decay = 0.01, temperature = 1e-3, lambda = 2,
+ * lr in {1, 0.1, 0.01}. beta1/beta2/adam_eps and alpha_comm are not printed
+ * in the paper; qqa_default_params fills 0.9/0.999/1e-8 and 0.3.
+ */
+typedef struct qqa_params {
+    int32_t S;            /* replicas, 1..1024 */
+    int32_t steps;        /* K: annealing steps; gamma sweeps over all K */
+    int32_t round_every;  /* periodic rounding period for the history (0 = final only) */
+    int32_t a_ent;        /* alpha-entropy exponent: 2, 4, 6 or 8 */
+    float lr, weight_decay, beta1, beta2, adam_eps;
+    float gamma_min, gamma_max;
+    float alpha_comm;     /* communication strength alpha of Eq. 10 */
+    float comm_eps;       /* STD_i = sqrt(var_i + comm_eps) */
+    float temperature;    /* Langevin temperature T */
+    float lambda;         /* penalty coefficient (MIS, clique) */
+    uint64_t seed;        /* Philox key for init and noise */
+    int32_t precision;    /* qqa_precision */
+    int32_t reserved;
+} qqa_params;
+
+/*
+ * Launch shape of the fused step kernel. Zero fields are chosen
+ * automatically from S_max and the precision.
+ *   group_lanes : lanes that share one node row (1, 2, 4, 8, 16, 32)
+ *   vec_per_lane: 16-byte vectors of replicas per lane (1, 2, 4, 8)
+ *     group_lanes * vec_per_lane * (4 FP32 | 8 BF16 replicas) >= S
+ *   block_threads: 32..256, multiple of 32
+ *   grid_blocks : persistent grid size (tiles are walked with a stride)
+ *   use_graphs  : capture chunks of steps as CUDA graphs and replay them
+ */
+typedef struct qqa_launch_config {
+    int32_t group_lanes;
+    int32_t vec_per_lane;
+    int32_t block_threads;
+    int32_t grid_blocks;
+    int32_t use_graphs;
+    int32_t reserved;
+} qqa_launch_config;
+
+typedef struct qqa_problem qqa_problem; /* device copy of one graph */
+typedef struct qqa_run qqa_run;         /* replica state of one or more instances */
+
+/* ---------------------------------------------------------------- misc */
+const char *qqa_last_error(void);
+const char *qqa_version(void);
+void qqa_default_params(qqa_params *out);
+/* Number of kernels this library has launched in this process (graph
+ * replays count every kernel node). */
+uint64_t qqa_launch_count(void);
+/* Number of SMs of the current device, or a negative error code. */
+int qqa_device_sm_count(void);
+
+/* ------------------------------------------------------------- problems */
+/*
+ * Copy a graph to the device (App. D.1: "adjacency matrix A; A_ij = edge weight").
+ *   kind     : qqa_kind
+ *   n        : nodes (>= 1)
+ *   row_ptr  : host int32[n+1], row_ptr[0] = 0, non-decreasing
+ *   col      : host int32[row_ptr[n]], each row strictly increasing, no self
+ *              loops, and symmetric (j in row i <=> i in row j)
+ *   w        : host int32[row_ptr[n]] edge weights (max-cut only, symmetric),
+ *              or NULL for unit weights; must be NULL for MIS / max-clique
+ * Errors: QQA_EINVAL for any violation above (checked on the host before any
+ * copy), QQA_ENOMEM, QQA_ECUDA.
+ */
+int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                       const int32_t *w, const qqa_allocator *alloc, void *stream, qqa_problem **out);
+int qqa_problem_info(const qqa_problem *p, int32_t *kind, int32_t *n, int64_t *nnz);
+void qqa_destroy_problem(qqa_problem *p);
+
+/* ----------------------------------------------------------------- runs */
+/*
+ * Create a run with room for `capacity` instances whose replica counts are at
+ * most S_max, all in `precision`. No instance is active yet. The step kernel
+ * layout is fixed here from (S_max, precision, cfg); cfg may be NULL.
+ * Device memory of the state is allocated per instance by qqa_run_add.
+ */
+int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
+                         const qqa_allocator *alloc, void *stream, qqa_run **out);
+/*
+ * Add one instance: allocate X (two buffers), the FP32 master (BF16 runs),
+ * AdamW moments m, v, and evaluation buffers; then draw the initial state
+ * p ~ U(0,1] from Philox (seed, node, replica) and zero m, v (step t = 0).
+ * The problem must outlive the run. Returns the slot index.
+ * Errors: QQA_EINVAL (S > S_max, bad params), QQA_EBUSY (no free slot), QQA_ENOMEM.
+ */
+int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void *stream, int32_t *slot);
+/*
+ * Restart one slot (slot >= 0) or every active slot (slot = -1) from a fresh
+ * initial state drawn with `seed` (step t = 0, m = v = 0, history cleared),
+ * keeping its allocations. Asynchronous except for a small descriptor upload.
+ */
+int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stream);
+/* Release one instance's state; its slot becomes free. Stream-ordered. */
+int qqa_run_remove(qqa_run *r, int32_t slot, void *stream);
+/* create_empty(count, max S) + add() for every problem, in order (slot k = problem k). */
+int qqa_run_create(qqa_problem *const *problems, const qqa_params *params, int32_t count,
+                   const qqa_launch_config *cfg, const qqa_allocator *alloc, void *stream, qqa_run **out);
+void qqa_run_destroy(qqa_run *r);
+/* Layout actually used (after auto choices). */
+int qqa_run_config(const qqa_run *r, qqa_launch_config *out);
+
+/*
+ * Advance every active, unfinished instance by up to `nsteps` annealing steps
+ * (one fused kernel launch per step; replayed from a CUDA graph when
+ * use_graphs is set). An instance stops at its own `steps`. Asynchronous.
+ */
+int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream);
+/*
+ * Projection rounding and exact costs of every replica of every active
+ * instance (asynchronous); appends each instance's best feasible objective to
+ * its history. Results are read with qqa_run_result after qqa_run_sync.
+ */
+int qqa_run_eval(qqa_run *r, void *stream);
+/* Wait for the stream, copy the latest evaluation to host mirrors, and check
+ * the device status word (QQA_ENONFINITE if a non-finite value was seen). */
+int qqa_run_sync(qqa_run *r, void *stream);
+/*
+ * Latest evaluation of one slot (after qqa_run_sync). Any pointer may be NULL.
+ *   obj, viol : int64[S]   objective (max units) and violation count
+ *               (MIS: edges inside x; clique: missing edges inside x; cut: 0)
+ *   feasible  : uint8[S]   viol == 0
+ *   energy    : double[S]  l(x) = -size + lambda*viol (MIS, clique); -cut (max-cut)
+ *   best_s    : feasible replica with the largest objective, ties -> lowest s; -1 if none
+ *   best_x    : uint32[ceil(n/32)] bit i%32 of word i/32 = x_i of replica best_s
+ *   step      : annealing steps completed when the evaluation ran
+ */
+int qqa_run_result(const qqa_run *r, int32_t slot, int64_t *obj, int64_t *viol, uint8_t *feasible,
+                   double *energy, int32_t *best_s, uint32_t *best_x, int32_t *step);
+/*
+ * Best feasible objective after each evaluation of a slot (INT64_MIN when no
+ * replica was feasible) and the step count it was taken at. `cap` entries at
+ * most; *count receives the number available. Reads host mirrors (after sync).
+ */
+int qqa_run_history(const qqa_run *r, int32_t slot, int32_t cap, int64_t *best_obj, int32_t *at_step,
+                    int32_t *count);
+/* Steps completed by a slot (host mirror, exact). */
+int qqa_run_slot_step(const qqa_run *r, int32_t slot, int32_t *t);
+
+/*
+ * Whole anneal of a batch, as the paper runs it: create the run, init, K
+ * steps with a periodic evaluation every round_every steps, and a final
+ * evaluation; then synchronise. The run stays alive for reading results.
+ */
+int qqa_anneal(qqa_problem *const *problems, const qqa_params *params, int32_t count,
+               const qqa_launch_config *cfg, const qqa_allocator *alloc, void *stream, qqa_run **out);
+/*
+ * Evaluate (qqa_run_eval + qqa_run_sync) and copy the results of every active
+ * slot, concatenated in slot order: obj/viol/feasible/energy have sum(S_k)
+ * entries, best_s has one per slot, best_x sum(ceil(n_k/32)) words.
+ */
+int qqa_round_eval(qqa_run *r, void *stream, int64_t *obj, int64_t *viol, uint8_t *feasible, double *energy,
+                   int32_t *best_s, uint32_t *best_x);
+
+/* --------------------------------------------------------- state / debug */
+/*
+ * Copy one slot's state to host FP32 arrays [n][S]: X = the state p (the FP32
+ * master in BF16 runs), m, v (AdamW moments, widened from BF16 in BF16 runs),
+ * and the step count t. Any array pointer may be NULL. Synchronises.
+ */
+int qqa_run_get_state(qqa_run *r, int32_t slot, void *stream, float *X, float *m, float *v, int32_t *t);
+/*
+ * Overwrite one slot's state from host FP32 arrays [n][S] (values of X must
+ * lie in [0,1]) and set its step count to t (0 <= t <= steps). BF16 runs
+ * keep X as the FP32 master and round it (and m, v) to BF16 storage.
+ * Checkpoint/resume: set_state(get_state()) continues bit-identically.
+ */
+int qqa_run_set_state(qqa_run *r, int32_t slot, void *stream, const float *X, const float *m, const float *v,
+                      int32_t t);
+/*
+ * One step of every active instance that also writes the gradient g of slot
+ * `slot` (all terms, before AdamW) to host grad[n][S]. Synchronises.
+ */
+int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QQA_H */

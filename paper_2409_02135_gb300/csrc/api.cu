@@ -1,0 +1,902 @@
+// api.cu -- host side of libqqa: the C ABI declared in include/qqa.h.
+//
+// A qqa_problem is a validated device copy of one CSR graph. A qqa_run is a
+// table of instance slots (one InstDesc per slot in device memory), the list
+// of (slot, row-block) tiles the fused step kernel walks, and the CUDA graphs
+// that replay chunks of steps. Every step of the method runs in the kernels of
+// step_*.cu and aux_kernels.cu; this file validates arguments, allocates,
+// builds descriptors and tiles, and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <atomic>
+#include <vector>
+
+#include "../../include/qqa.h"
+#include "qqa_internal.cuh"
+
+namespace qqa {
+using StepFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t);
+StepFn step_kernel_fp32(int G, int VPL);
+StepFn step_kernel_bf16(int G, int VPL);
+}  // namespace qqa
+
+using namespace qqa;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define QQA_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(QQA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define QQA_CK_LAUNCH(what)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                  \
+        if (e_ != cudaSuccess) return fail(QQA_ECUDA, "%s launch: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+// --------------------------------------------------------------- allocator
+struct Alloc {
+    qqa_allocator user{};
+    bool has_user = false;
+    void *get(size_t bytes, cudaStream_t st)
+    {
+        if (bytes == 0) bytes = 16;
+        if (has_user) return user.alloc(bytes, (void *)st, user.ctx);
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void put(void *p, cudaStream_t st)
+    {
+        if (!p) return;
+        if (has_user) user.free(p, (void *)st, user.ctx);
+        else cudaFree(p);
+    }
+    static Alloc from(const qqa_allocator *a)
+    {
+        Alloc r;
+        if (a && a->alloc && a->free) {
+            r.user = *a;
+            r.has_user = true;
+        }
+        return r;
+    }
+};
+
+struct qqa_problem {
+    int32_t kind = 0, n = 0;
+    int64_t nnz = 0;
+    int32_t *row_ptr = nullptr, *col = nullptr, *w = nullptr;
+    Alloc alloc;
+};
+
+// ------------------------------------------------------------------- misc
+extern "C" const char *qqa_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *qqa_version(void) { return "qqa-gb300 0.1 (sm_103a)"; }
+extern "C" uint64_t qqa_launch_count(void) { return g_launches.load(); }
+
+extern "C" void qqa_default_params(qqa_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->S = 128;
+    p->steps = 3000;
+    p->round_every = 50;
+    p->a_ent = 4;
+    p->lr = 0.1f;
+    p->weight_decay = 0.01f;
+    p->beta1 = 0.9f;
+    p->beta2 = 0.999f;
+    p->adam_eps = 1e-8f;
+    p->gamma_min = -2.0f;
+    p->gamma_max = 0.1f;
+    p->alpha_comm = 0.3f;
+    p->comm_eps = 1e-8f;
+    p->temperature = 1e-3f;
+    p->lambda = 2.0f;
+    p->seed = 0;
+    p->precision = QQA_FP32;
+}
+
+extern "C" int qqa_device_sm_count(void)
+{
+    int dev = 0, sms = 0;
+    QQA_CK(cudaGetDevice(&dev));
+    QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+// --------------------------------------------------------------- problems
+static int validate_csr(int32_t kind, int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w)
+{
+    if (kind < QQA_MIS || kind > QQA_MAXCLIQUE) return fail(QQA_EINVAL, "unknown problem kind %d", kind);
+    if (n < 1) return fail(QQA_EINVAL, "n must be >= 1 (got %d)", n);
+    if (!rp) return fail(QQA_EINVAL, "row_ptr is NULL");
+    if (rp[0] != 0) return fail(QQA_EINVAL, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return fail(QQA_EINVAL, "row_ptr decreases at row %d", i);
+    const int64_t nnz = rp[n];
+    if (nnz > 0 && !col) return fail(QQA_EINVAL, "col is NULL");
+    if (w && kind != QQA_MAXCUT) return fail(QQA_EINVAL, "edge weights are only defined for max-cut");
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int32_t j = col[k];
+            if (j < 0 || j >= n) return fail(QQA_EINVAL, "col[%lld] = %d out of range [0, %d)", (long long)k, j, n);
+            if (j == i) return fail(QQA_EINVAL, "self-loop at node %d", i);
+            if (k > rp[i] && col[k - 1] >= j) return fail(QQA_EINVAL, "row %d not strictly increasing", i);
+            // symmetry: i must appear in row j (binary search)
+            const int32_t *b = col + rp[j], *e = col + rp[j + 1];
+            const int32_t *f = std::lower_bound(b, e, i);
+            if (f == e || *f != i) return fail(QQA_EINVAL, "edge (%d,%d) has no reverse entry", i, j);
+            if (w && w[k] != w[f - col]) return fail(QQA_EINVAL, "weight of (%d,%d) differs from (%d,%d)", i, j, j, i);
+        }
+    }
+    return QQA_OK;
+}
+
+extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                  const int32_t *w, const qqa_allocator *alloc, void *stream, qqa_problem **out)
+{
+    if (!out) return fail(QQA_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_csr(kind, n, row_ptr, col, w);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    qqa_problem *p = new (std::nothrow) qqa_problem();
+    if (!p) return fail(QQA_ENOMEM, "host allocation failed");
+    p->kind = kind;
+    p->n = n;
+    p->nnz = row_ptr[n];
+    p->alloc = Alloc::from(alloc);
+    p->row_ptr = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)(n + 1), st);
+    p->col = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
+    if (w) p->w = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
+    if (!p->row_ptr || !p->col || (w && !p->w)) {
+        qqa_destroy_problem(p);
+        return fail(QQA_ENOMEM, "device allocation for the graph failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(p->row_ptr, row_ptr, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && p->nnz)
+        e = cudaMemcpyAsync(p->col, col, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && w && p->nnz)
+        e = cudaMemcpyAsync(p->w, w, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host arrays may be freed after return
+    if (e != cudaSuccess) {
+        qqa_destroy_problem(p);
+        return fail(QQA_ECUDA, "graph upload: %s", cudaGetErrorString(e));
+    }
+    *out = p;
+    return QQA_OK;
+}
+
+extern "C" int qqa_problem_info(const qqa_problem *p, int32_t *kind, int32_t *n, int64_t *nnz)
+{
+    if (!p) return fail(QQA_EINVAL, "problem is NULL");
+    if (kind) *kind = p->kind;
+    if (n) *n = p->n;
+    if (nnz) *nnz = p->nnz;
+    return QQA_OK;
+}
+
+extern "C" void qqa_destroy_problem(qqa_problem *p)
+{
+    if (!p) return;
+    p->alloc.put(p->row_ptr, 0);
+    p->alloc.put(p->col, 0);
+    p->alloc.put(p->w, 0);
+    delete p;
+}
+
+// -------------------------------------------------------------------- runs
+struct SlotHost {
+    bool active = false;
+    const qqa_problem *prob = nullptr;
+    qqa_params prm{};
+    int32_t n = 0, S = 0, S_pad = 0, W = 0, K = 0;
+    int32_t t = 0;            // exact host mirror of the device step counter
+    int32_t last_eval_t = -1; // host mirror of the evaluation rule
+    int32_t hist_cap = 0;
+    std::vector<void *> dev;  // device allocations of this slot
+    // host mirrors of the latest evaluation (filled by qqa_run_sync)
+    std::vector<long long> obj, viol;
+    std::vector<uint8_t> feas;
+    std::vector<double> energy;
+    int32_t best = -1, eval_step = -1, eval_count = 0;
+};
+
+struct qqa_run {
+    int32_t capacity = 0, S_max = 0, S_max_pad = 0, prec = 0, vec = 4;
+    qqa_launch_config cfg{};
+    int32_t rows_per_tile = 0, max_grid = 0, smem = 0;
+    StepFn step_fn = nullptr;
+    Alloc alloc;
+    InstDesc *d_descs = nullptr;
+    std::vector<InstDesc> h_descs;
+    Tile *d_tiles = nullptr;
+    int32_t tile_cap = 0;
+    int32_t *d_num_tiles = nullptr;
+    int32_t num_tiles = 0;
+    RunStatus *d_status = nullptr;
+    float *d_scratch = nullptr;   // state import/export staging
+    size_t scratch_bytes = 0;
+    std::vector<SlotHost> slots;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+};
+
+static int pick_layout(int32_t S_pad, int32_t vec, int32_t &G, int32_t &VPL)
+{
+    const int nvec = S_pad / vec;
+    if (nvec <= 32) {
+        G = 1;
+        while (G < nvec) G <<= 1;
+        VPL = 1;
+    } else {
+        G = 32;
+        VPL = 1;
+        while (G * VPL < nvec) VPL <<= 1;
+    }
+    return QQA_OK;
+}
+
+static int resolve_config(qqa_run *r, const qqa_launch_config *cfg)
+{
+    qqa_launch_config c{};
+    if (cfg) c = *cfg;
+    int32_t G = c.group_lanes, VPL = c.vec_per_lane;
+    if (G == 0 || VPL == 0) {
+        int32_t g2, v2;
+        pick_layout(r->S_max_pad, r->vec, g2, v2);
+        if (G == 0 && VPL == 0) { G = g2; VPL = v2; }
+        else if (G == 0) { G = 1; while (G < 32 && G * VPL * r->vec < r->S_max_pad) G <<= 1; }
+        else { VPL = 1; while (G * VPL * r->vec < r->S_max_pad) VPL <<= 1; }
+    }
+    if (G * VPL * r->vec < r->S_max_pad)
+        return fail(QQA_EINVAL, "layout G=%d VPL=%d covers %d replicas < %d", G, VPL, G * VPL * r->vec, r->S_max_pad);
+    r->step_fn = r->prec == kFP32 ? step_kernel_fp32(G, VPL) : step_kernel_bf16(G, VPL);
+    if (!r->step_fn) return fail(QQA_EINVAL, "no step kernel for G=%d VPL=%d precision %d", G, VPL, r->prec);
+    int block = c.block_threads ? c.block_threads : 256;
+    if (block < 32 || block > 256 || block % 32) return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
+    c.group_lanes = G;
+    c.vec_per_lane = VPL;
+    c.block_threads = block;
+    r->rows_per_tile = (block / 32) * (32 / G);
+    r->smem = r->S_max_pad * (int)sizeof(float);
+    int dev = 0, sms = 0, occ = 0;
+    QQA_CK(cudaGetDevice(&dev));
+    QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block, r->smem));
+    if (occ < 1) return fail(QQA_EINVAL, "step kernel G=%d VPL=%d cannot run %d threads per block", G, VPL, block);
+    r->max_grid = c.grid_blocks ? c.grid_blocks : sms * occ;
+    c.grid_blocks = r->max_grid;
+    r->cfg = c;
+    return QQA_OK;
+}
+
+static int upload_desc(qqa_run *r, int32_t slot, cudaStream_t st)
+{
+    // the device advances t and last_eval_t itself; the host mirrors follow the
+    // same rules exactly, so re-uploading a descriptor never moves them
+    r->h_descs[slot].t = r->slots[slot].t;
+    r->h_descs[slot].last_eval_t = r->slots[slot].last_eval_t;
+    QQA_CK(cudaMemcpyAsync(r->d_descs + slot, &r->h_descs[slot], sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaStreamSynchronize(st));  // the host mirror may change again right after
+    return QQA_OK;
+}
+
+static void drop_graphs(qqa_run *r)
+{
+    for (auto &kv : r->graphs) cudaGraphExecDestroy(kv.second);
+    r->graphs.clear();
+}
+
+static int rebuild_tiles(qqa_run *r, cudaStream_t st)
+{
+    std::vector<Tile> tiles;
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        const SlotHost &s = r->slots[k];
+        if (!s.active) continue;
+        for (int32_t row0 = 0; row0 < s.n; row0 += r->rows_per_tile) tiles.push_back(Tile{k, row0});
+    }
+    const int32_t nt = (int32_t)tiles.size();
+    if (nt > r->tile_cap) {
+        int32_t cap = std::max<int32_t>(nt, 2 * r->tile_cap);
+        QQA_CK(cudaStreamSynchronize(st));
+        Tile *nt_buf = (Tile *)r->alloc.get(sizeof(Tile) * (size_t)cap, st);
+        if (!nt_buf) return fail(QQA_ENOMEM, "tile list allocation failed");
+        r->alloc.put(r->d_tiles, st);
+        r->d_tiles = nt_buf;
+        r->tile_cap = cap;
+        drop_graphs(r);  // captured graphs hold the old tile pointer
+    }
+    if (nt) QQA_CK(cudaMemcpyAsync(r->d_tiles, tiles.data(), sizeof(Tile) * (size_t)nt, cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, &nt, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaStreamSynchronize(st));
+    r->num_tiles = nt;
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
+                                    const qqa_allocator *alloc, void *stream, qqa_run **out)
+{
+    if (!out) return fail(QQA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (capacity < 1) return fail(QQA_EINVAL, "capacity must be >= 1");
+    if (precision != QQA_FP32 && precision != QQA_BF16) return fail(QQA_EINVAL, "unknown precision %d", precision);
+    if (S_max < 1 || S_max > 1024) return fail(QQA_EINVAL, "S_max must be in [1, 1024] (got %d)", S_max);
+    cudaStream_t st = (cudaStream_t)stream;
+    qqa_run *r = new (std::nothrow) qqa_run();
+    if (!r) return fail(QQA_ENOMEM, "host allocation failed");
+    r->capacity = capacity;
+    r->prec = precision;
+    r->vec = precision == QQA_FP32 ? 4 : 8;
+    r->S_max = S_max;
+    r->S_max_pad = (S_max + r->vec - 1) / r->vec * r->vec;
+    r->alloc = Alloc::from(alloc);
+    int rc = resolve_config(r, cfg);
+    if (rc) { delete r; return rc; }
+    r->h_descs.assign(capacity, InstDesc{});
+    r->slots.resize(capacity);
+    r->d_descs = (InstDesc *)r->alloc.get(sizeof(InstDesc) * (size_t)capacity, st);
+    r->d_num_tiles = (int32_t *)r->alloc.get(sizeof(int32_t), st);
+    r->d_status = (RunStatus *)r->alloc.get(sizeof(RunStatus), st);
+    if (!r->d_descs || !r->d_num_tiles || !r->d_status) {
+        qqa_run_destroy(r);
+        return fail(QQA_ENOMEM, "run allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)capacity,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_status, 0, sizeof(RunStatus), st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        qqa_run_destroy(r);
+        return fail(QQA_ECUDA, "run setup: %s", cudaGetErrorString(e));
+    }
+    *out = r;
+    return QQA_OK;
+}
+
+static int check_params(const qqa_params *p, int32_t S_max, int32_t prec)
+{
+    if (!p) return fail(QQA_EINVAL, "params is NULL");
+    if (p->S < 1 || p->S > S_max) return fail(QQA_EINVAL, "S = %d outside [1, %d]", p->S, S_max);
+    if (p->steps < 1) return fail(QQA_EINVAL, "steps must be >= 1");
+    if (p->round_every < 0) return fail(QQA_EINVAL, "round_every must be >= 0");
+    if (p->a_ent < 2 || p->a_ent > 8 || p->a_ent % 2) return fail(QQA_EINVAL, "a_ent must be 2, 4, 6 or 8");
+    if (!(p->lr > 0.0f) || !std::isfinite(p->lr)) return fail(QQA_EINVAL, "lr must be positive and finite");
+    if (!(p->beta1 >= 0.5f && p->beta1 < 1.0f) || !(p->beta2 >= 0.5f && p->beta2 < 1.0f))
+        return fail(QQA_EINVAL, "beta1, beta2 must lie in [0.5, 1)");
+    if (!(p->adam_eps > 0.0f) || !(p->comm_eps >= 0.0f) || !(p->temperature >= 0.0f) || !(p->weight_decay >= 0.0f))
+        return fail(QQA_EINVAL, "adam_eps > 0 and comm_eps, temperature, weight_decay >= 0 required");
+    if (!std::isfinite(p->gamma_min) || !std::isfinite(p->gamma_max) || !std::isfinite(p->alpha_comm) ||
+        !std::isfinite(p->lambda))
+        return fail(QQA_EINVAL, "gamma, alpha_comm and lambda must be finite");
+    if (p->alpha_comm != 0.0f && !(p->comm_eps > 0.0f)) return fail(QQA_EINVAL, "alpha_comm != 0 needs comm_eps > 0");
+    if (p->precision != prec) return fail(QQA_EINVAL, "instance precision %d differs from the run's %d", p->precision, prec);
+    return QQA_OK;
+}
+
+static void free_slot(qqa_run *r, int32_t k, cudaStream_t st)
+{
+    SlotHost &s = r->slots[k];
+    for (void *p : s.dev) r->alloc.put(p, st);
+    s = SlotHost{};
+    r->h_descs[k] = InstDesc{};
+}
+
+extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void *stream, int32_t *slot_out)
+{
+    if (!r || !prob) return fail(QQA_EINVAL, "run or problem is NULL");
+    int rc = check_params(prm, r->S_max, r->prec);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t k = -1;
+    for (int32_t i = 0; i < r->capacity; ++i)
+        if (!r->slots[i].active) { k = i; break; }
+    if (k < 0) return fail(QQA_EBUSY, "no free slot (capacity %d)", r->capacity);
+
+    SlotHost &s = r->slots[k];
+    s = SlotHost{};
+    s.prob = prob;
+    s.prm = *prm;
+    s.n = prob->n;
+    s.S = prm->S;
+    s.S_pad = (prm->S + r->vec - 1) / r->vec * r->vec;
+    s.W = (prm->S + 31) / 32;
+    s.K = prm->steps;
+    s.hist_cap = (prm->round_every > 0 ? prm->steps / prm->round_every : 0) + 2;
+    const size_t elems = (size_t)s.n * s.S_pad;
+    const size_t tb = r->prec == kFP32 ? 4 : 2;
+    auto get = [&](size_t bytes) -> void * {
+        void *p = r->alloc.get(bytes, st);
+        if (p) s.dev.push_back(p);
+        return p;
+    };
+    InstDesc d{};
+    d.row_ptr = prob->row_ptr;
+    d.col = prob->col;
+    d.w = prob->w;
+    d.X[0] = get(elems * tb);
+    d.X[1] = get(elems * tb);
+    d.master = r->prec == kBF16 ? (float *)get(elems * 4) : nullptr;
+    d.m = get(elems * tb);
+    d.v = get(elems * tb);
+    d.colsum = prob->kind == QQA_MAXCLIQUE ? (float *)get(3 * (size_t)s.S_pad * 4) : nullptr;
+    d.grad_dbg = nullptr;
+    d.bits = (uint32_t *)get((size_t)s.n * s.W * 4);
+    d.counts = (unsigned long long *)get(3 * (size_t)s.S_pad * 8);
+    d.res_obj = (long long *)get((size_t)s.S_pad * 8);
+    d.res_viol = (long long *)get((size_t)s.S_pad * 8);
+    d.res_feas = (uint8_t *)get((size_t)s.S_pad);
+    d.res_energy = (double *)get((size_t)s.S_pad * 8);
+    d.res_meta = (int32_t *)get(4 * 4);
+    d.res_bestx = (uint32_t *)get((size_t)((s.n + 31) / 32) * 4);
+    d.hist_best = (long long *)get((size_t)s.hist_cap * 8);
+    d.hist_step = (int32_t *)get((size_t)s.hist_cap * 4);
+    bool ok = d.X[0] && d.X[1] && d.m && d.v && d.bits && d.counts && d.res_obj && d.res_viol && d.res_feas &&
+              d.res_energy && d.res_meta && d.res_bestx && d.hist_best && d.hist_step &&
+              (r->prec == kFP32 || d.master) && (prob->kind != QQA_MAXCLIQUE || d.colsum);
+    if (!ok) {
+        free_slot(r, k, st);
+        return fail(QQA_ENOMEM, "device allocation for instance state failed (n=%d, S=%d)", s.n, s.S);
+    }
+    d.n = s.n;
+    d.S = s.S;
+    d.S_pad = s.S_pad;
+    d.W = s.W;
+    d.kind = prob->kind;
+    d.a_ent = prm->a_ent;
+    d.t = 0;
+    d.K = prm->steps;
+    d.active = 1;
+    d.hist_cap = s.hist_cap;
+    d.last_eval_t = -1;
+    d.lr = prm->lr;
+    d.wd = prm->weight_decay;
+    d.b1 = prm->beta1;
+    d.b2 = prm->beta2;
+    d.adam_eps = prm->adam_eps;
+    d.gmin = prm->gamma_min;
+    d.gmax = prm->gamma_max;
+    d.alpha = prm->alpha_comm;
+    d.comm_eps = prm->comm_eps;
+    d.noise_scale = (float)std::sqrt(2.0 * (double)prm->lr * (double)prm->temperature);
+    d.lambda = prm->lambda;
+    d.seed_lo = (uint32_t)(prm->seed & 0xffffffffu);
+    d.seed_hi = (uint32_t)(prm->seed >> 32);
+    r->h_descs[k] = d;
+    s.active = true;
+    s.obj.assign(s.S, 0);
+    s.viol.assign(s.S, 0);
+    s.feas.assign(s.S, 0);
+    s.energy.assign(s.S, 0.0);
+    cudaError_t e = cudaMemsetAsync(d.res_meta, 0, 16, st);
+    if (e != cudaSuccess) { free_slot(r, k, st); return fail(QQA_ECUDA, "memset: %s", cudaGetErrorString(e)); }
+    rc = upload_desc(r, k, st);
+    if (rc) { free_slot(r, k, st); return rc; }
+    launch_init(r->d_descs, k, s.n, s.S_pad, r->prec, st);
+    g_launches += 1;
+    if (prob->kind == QQA_MAXCLIQUE) {
+        launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+        g_launches += 1;
+    }
+    QQA_CK_LAUNCH("init");
+    rc = rebuild_tiles(r, st);
+    if (rc) return rc;
+    if (slot_out) *slot_out = k;
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stream)
+{
+    if (!r) return fail(QQA_EINVAL, "run is NULL");
+    if (slot < -1 || slot >= r->capacity || (slot >= 0 && !r->slots[slot].active))
+        return fail(QQA_EINVAL, "bad slot %d", slot);
+    cudaStream_t st = (cudaStream_t)stream;
+    bool any = false;
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        if ((slot >= 0 && k != slot) || !r->slots[k].active) continue;
+        SlotHost &s = r->slots[k];
+        s.t = 0;
+        s.last_eval_t = -1;
+        s.eval_count = 0;
+        s.prm.seed = seed;
+        r->h_descs[k].seed_lo = (uint32_t)(seed & 0xffffffffu);
+        r->h_descs[k].seed_hi = (uint32_t)(seed >> 32);
+        any = true;
+    }
+    if (!any) return QQA_OK;
+    // one upload of the whole table (reset slots changed t, seed, eval marker)
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        r->h_descs[k].t = r->slots[k].t;
+        r->h_descs[k].last_eval_t = r->slots[k].last_eval_t;
+    }
+    QQA_CK(cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)r->capacity,
+                           cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaStreamSynchronize(st));
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        if ((slot >= 0 && k != slot) || !r->slots[k].active) continue;
+        const SlotHost &s = r->slots[k];
+        QQA_CK(cudaMemsetAsync(r->h_descs[k].res_meta, 0, 16, st));
+        launch_init(r->d_descs, k, s.n, s.S_pad, r->prec, st);
+        g_launches += 1;
+        if (s.prob->kind == QQA_MAXCLIQUE) {
+            launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+            g_launches += 1;
+        }
+    }
+    QQA_CK_LAUNCH("reset");
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_remove(qqa_run *r, int32_t k, void *stream)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    cudaStream_t st = (cudaStream_t)stream;
+    r->h_descs[k].active = 0;
+    int rc = upload_desc(r, k, st);
+    if (rc) return rc;
+    QQA_CK(cudaStreamSynchronize(st));
+    free_slot(r, k, st);
+    return rebuild_tiles(r, st);
+}
+
+extern "C" int qqa_run_create(qqa_problem *const *problems, const qqa_params *params, int32_t count,
+                              const qqa_launch_config *cfg, const qqa_allocator *alloc, void *stream, qqa_run **out)
+{
+    if (!problems || !params || count < 1) return fail(QQA_EINVAL, "need count >= 1 problems and params");
+    int32_t S_max = 1;
+    for (int32_t k = 0; k < count; ++k) S_max = std::max(S_max, params[k].S);
+    if (S_max > 1024) return fail(QQA_EINVAL, "S = %d exceeds 1024", S_max);
+    qqa_run *r = nullptr;
+    int rc = qqa_run_create_empty(count, S_max, params[0].precision, cfg, alloc, stream, &r);
+    if (rc) return rc;
+    for (int32_t k = 0; k < count; ++k) {
+        int32_t slot = -1;
+        rc = qqa_run_add(r, problems[k], &params[k], stream, &slot);
+        if (rc) {
+            std::string msg = g_last_error;
+            qqa_run_destroy(r);
+            return fail(rc, "instance %d: %s", k, msg.c_str());
+        }
+    }
+    *out = r;
+    return QQA_OK;
+}
+
+extern "C" void qqa_run_destroy(qqa_run *r)
+{
+    if (!r) return;
+    cudaDeviceSynchronize();
+    drop_graphs(r);
+    for (int32_t k = 0; k < (int32_t)r->slots.size(); ++k)
+        if (r->slots[k].active) free_slot(r, k, 0);
+    r->alloc.put(r->d_descs, 0);
+    r->alloc.put(r->d_tiles, 0);
+    r->alloc.put(r->d_num_tiles, 0);
+    r->alloc.put(r->d_status, 0);
+    r->alloc.put(r->d_scratch, 0);
+    if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+    delete r;
+}
+
+extern "C" int qqa_run_config(const qqa_run *r, qqa_launch_config *out)
+{
+    if (!r || !out) return fail(QQA_EINVAL, "NULL argument");
+    *out = r->cfg;
+    return QQA_OK;
+}
+
+// ------------------------------------------------------------------- steps
+static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream_t st)
+{
+    for (int32_t i = 0; i < chunk; ++i) {
+        r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles, r->d_status, i);
+    }
+    launch_advance(r->d_descs, r->capacity, chunk, st);
+    QQA_CK_LAUNCH("step");
+    return QQA_OK;
+}
+
+static int get_graph(qqa_run *r, int32_t chunk, int32_t grid, cudaGraphExec_t *exec)
+{
+    auto key = std::make_pair(chunk, grid);
+    auto it = r->graphs.find(key);
+    if (it != r->graphs.end()) { *exec = it->second; return QQA_OK; }
+    cudaGraph_t g = nullptr;
+    QQA_CK(cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step_chunk(r, chunk, grid, r->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(r->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(QQA_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(QQA_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    r->graphs[key] = ge;
+    *exec = ge;
+    return QQA_OK;
+}
+
+static const int32_t kGraphChunk = 50;
+
+extern "C" int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream)
+{
+    if (!r) return fail(QQA_EINVAL, "run is NULL");
+    if (nsteps < 0) return fail(QQA_EINVAL, "nsteps < 0");
+    if (nsteps == 0 || r->num_tiles == 0) return QQA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t grid = std::min(r->max_grid, r->num_tiles);
+    int32_t left = nsteps;
+    while (left > 0) {
+        const int32_t chunk = std::min(left, kGraphChunk);
+        if (r->cfg.use_graphs && chunk == kGraphChunk) {
+            cudaGraphExec_t ge = nullptr;
+            int rc = get_graph(r, chunk, grid, &ge);
+            if (rc) return rc;
+            QQA_CK(cudaGraphLaunch(ge, st));
+        } else {
+            int rc = launch_step_chunk(r, chunk, grid, st);
+            if (rc) return rc;
+        }
+        g_launches += (unsigned long long)chunk + 1;
+        for (auto &s : r->slots)
+            if (s.active) s.t = std::min(s.t + chunk, s.K);
+        left -= chunk;
+    }
+    return QQA_OK;
+}
+
+// -------------------------------------------------------------------- eval
+extern "C" int qqa_run_eval(qqa_run *r, void *stream)
+{
+    if (!r) return fail(QQA_EINVAL, "run is NULL");
+    if (r->num_tiles == 0) return QQA_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t grid = std::min(r->max_grid, r->num_tiles);
+    launch_eval(r->d_descs, r->d_tiles, r->d_num_tiles, grid, r->rows_per_tile, r->capacity, r->S_max_pad, r->prec, st);
+    g_launches += 3;
+    QQA_CK_LAUNCH("eval");
+    for (auto &s : r->slots)
+        if (s.active && s.t != s.last_eval_t) s.last_eval_t = s.t;
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_sync(qqa_run *r, void *stream)
+{
+    if (!r) return fail(QQA_EINVAL, "run is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    QQA_CK(cudaStreamSynchronize(st));
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        SlotHost &s = r->slots[k];
+        if (!s.active) continue;
+        const InstDesc &d = r->h_descs[k];
+        int32_t meta[4] = {0, 0, 0, 0};
+        QQA_CK(cudaMemcpy(meta, d.res_meta, sizeof meta, cudaMemcpyDeviceToHost));
+        if (meta[2] == 0) continue;  // never evaluated
+        QQA_CK(cudaMemcpy(s.obj.data(), d.res_obj, sizeof(long long) * s.S, cudaMemcpyDeviceToHost));
+        QQA_CK(cudaMemcpy(s.viol.data(), d.res_viol, sizeof(long long) * s.S, cudaMemcpyDeviceToHost));
+        QQA_CK(cudaMemcpy(s.feas.data(), d.res_feas, s.S, cudaMemcpyDeviceToHost));
+        QQA_CK(cudaMemcpy(s.energy.data(), d.res_energy, sizeof(double) * s.S, cudaMemcpyDeviceToHost));
+        s.best = meta[0];
+        s.eval_step = meta[1];
+        s.eval_count = meta[2];
+    }
+    RunStatus stt{};
+    QQA_CK(cudaMemcpy(&stt, r->d_status, sizeof stt, cudaMemcpyDeviceToHost));
+    if (stt.nonfinite) return fail(QQA_ENONFINITE, "%llu non-finite gradient/state values were produced", stt.nonfinite);
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_result(const qqa_run *r, int32_t k, int64_t *obj, int64_t *viol, uint8_t *feasible,
+                              double *energy, int32_t *best_s, uint32_t *best_x, int32_t *step)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    const SlotHost &s = r->slots[k];
+    if (s.eval_count == 0) return fail(QQA_EBUSY, "slot %d has no synchronised evaluation", k);
+    if (obj) for (int i = 0; i < s.S; ++i) obj[i] = s.obj[i];
+    if (viol) for (int i = 0; i < s.S; ++i) viol[i] = s.viol[i];
+    if (feasible) std::memcpy(feasible, s.feas.data(), s.S);
+    if (energy) std::memcpy(energy, s.energy.data(), sizeof(double) * s.S);
+    if (best_s) *best_s = s.best;
+    if (step) *step = s.eval_step;
+    if (best_x) QQA_CK(cudaMemcpy(best_x, r->h_descs[k].res_bestx, sizeof(uint32_t) * ((s.n + 31) / 32),
+                                  cudaMemcpyDeviceToHost));
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_history(const qqa_run *r, int32_t k, int32_t cap, int64_t *best_obj, int32_t *at_step,
+                               int32_t *count)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    const SlotHost &s = r->slots[k];
+    const int32_t avail = std::min(s.eval_count, s.hist_cap);
+    const int32_t m = std::min(avail, std::max(cap, 0));
+    if (count) *count = avail;
+    if (m > 0 && best_obj)
+        QQA_CK(cudaMemcpy(best_obj, r->h_descs[k].hist_best, sizeof(long long) * m, cudaMemcpyDeviceToHost));
+    if (m > 0 && at_step)
+        QQA_CK(cudaMemcpy(at_step, r->h_descs[k].hist_step, sizeof(int32_t) * m, cudaMemcpyDeviceToHost));
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_slot_step(const qqa_run *r, int32_t k, int32_t *t)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    if (t) *t = r->slots[k].t;
+    return QQA_OK;
+}
+
+extern "C" int qqa_anneal(qqa_problem *const *problems, const qqa_params *params, int32_t count,
+                          const qqa_launch_config *cfg, const qqa_allocator *alloc, void *stream, qqa_run **out)
+{
+    qqa_run *r = nullptr;
+    int rc = qqa_run_create(problems, params, count, cfg, alloc, stream, &r);
+    if (rc) return rc;
+    int32_t kmax = 0, re = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        kmax = std::max(kmax, params[k].steps);
+        if (params[k].round_every > 0) re = re ? std::min(re, params[k].round_every) : params[k].round_every;
+    }
+    int32_t done = 0;
+    while (done < kmax) {
+        const int32_t chunk = re > 0 ? std::min(re, kmax - done) : kmax - done;
+        rc = qqa_run_steps(r, chunk, stream);
+        if (!rc) {
+            done += chunk;
+            if (re > 0) rc = qqa_run_eval(r, stream);   // periodic rounding (the last one is the final)
+        }
+        if (rc) { qqa_run_destroy(r); return rc; }
+    }
+    if (re == 0) rc = qqa_run_eval(r, stream);
+    if (!rc) rc = qqa_run_sync(r, stream);
+    if (rc && rc != QQA_ENONFINITE) { qqa_run_destroy(r); return rc; }
+    *out = r;
+    return rc;
+}
+
+extern "C" int qqa_round_eval(qqa_run *r, void *stream, int64_t *obj, int64_t *viol, uint8_t *feasible,
+                              double *energy, int32_t *best_s, uint32_t *best_x)
+{
+    int rc = qqa_run_eval(r, stream);
+    if (rc) return rc;
+    rc = qqa_run_sync(r, stream);
+    if (rc && rc != QQA_ENONFINITE) return rc;
+    const int rc_sync = rc;
+    size_t off = 0, boff = 0;
+    int32_t j = 0;
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        const SlotHost &s = r->slots[k];
+        if (!s.active) continue;
+        rc = qqa_run_result(r, k, obj ? obj + off : nullptr, viol ? viol + off : nullptr,
+                            feasible ? feasible + off : nullptr, energy ? energy + off : nullptr,
+                            best_s ? best_s + j : nullptr, best_x ? best_x + boff : nullptr, nullptr);
+        if (rc) return rc;
+        off += (size_t)s.S;
+        boff += (size_t)((s.n + 31) / 32);
+        ++j;
+    }
+    return rc_sync;
+}
+
+// ------------------------------------------------------------ state / debug
+static int ensure_scratch(qqa_run *r, size_t bytes, cudaStream_t st)
+{
+    if (r->scratch_bytes >= bytes) return QQA_OK;
+    QQA_CK(cudaStreamSynchronize(st));
+    r->alloc.put(r->d_scratch, st);
+    r->d_scratch = (float *)r->alloc.get(bytes, st);
+    r->scratch_bytes = r->d_scratch ? bytes : 0;
+    if (!r->d_scratch) return fail(QQA_ENOMEM, "staging allocation of %zu bytes failed", bytes);
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_get_state(qqa_run *r, int32_t k, void *stream, float *X, float *m, float *v, int32_t *t)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    cudaStream_t st = (cudaStream_t)stream;
+    const SlotHost &s = r->slots[k];
+    const size_t elems = (size_t)s.n * s.S;
+    int rc = ensure_scratch(r, elems * 4, st);
+    if (rc) return rc;
+    float *dst[3] = {X, m, v};
+    for (int which = 0; which < 3; ++which) {
+        if (!dst[which]) continue;
+        launch_pack_state(r->d_descs, k, s.n, s.S, s.S_pad, r->prec, which, r->d_scratch, st);
+        g_launches += 1;
+        QQA_CK_LAUNCH("pack_state");
+        QQA_CK(cudaMemcpyAsync(dst[which], r->d_scratch, elems * 4, cudaMemcpyDeviceToHost, st));
+        QQA_CK(cudaStreamSynchronize(st));
+    }
+    if (t) *t = s.t;
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_set_state(qqa_run *r, int32_t k, void *stream, const float *X, const float *m, const float *v,
+                                 int32_t t)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    if (!X || !m || !v) return fail(QQA_EINVAL, "X, m and v are required");
+    SlotHost &s = r->slots[k];
+    if (t < 0 || t > s.K) return fail(QQA_EINVAL, "t = %d outside [0, %d]", t, s.K);
+    const size_t elems = (size_t)s.n * s.S;
+    for (size_t e = 0; e < elems; ++e)
+        if (!(X[e] >= 0.0f && X[e] <= 1.0f)) return fail(QQA_EINVAL, "X[%zu] = %g outside [0, 1]", e, (double)X[e]);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_scratch(r, elems * 12, st);
+    if (rc) return rc;
+    QQA_CK(cudaMemcpyAsync(r->d_scratch, X, elems * 4, cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaMemcpyAsync(r->d_scratch + elems, m, elems * 4, cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaMemcpyAsync(r->d_scratch + 2 * elems, v, elems * 4, cudaMemcpyHostToDevice, st));
+    s.t = t;
+    s.last_eval_t = -1;
+    rc = upload_desc(r, k, st);
+    if (rc) return rc;
+    launch_unpack_state(r->d_descs, k, s.n, s.S, s.S_pad, r->prec, r->d_scratch, r->d_scratch + elems,
+                        r->d_scratch + 2 * elems, t, st);
+    g_launches += 1;
+    if (s.prob->kind == QQA_MAXCLIQUE) {
+        launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+        g_launches += 1;
+    }
+    QQA_CK_LAUNCH("set_state");
+    QQA_CK(cudaStreamSynchronize(st));
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_step_debug(qqa_run *r, int32_t k, void *stream, float *grad)
+{
+    if (!r || k < 0 || k >= r->capacity || !r->slots[k].active) return fail(QQA_EINVAL, "bad slot %d", k);
+    if (!grad) return fail(QQA_EINVAL, "grad is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    SlotHost &s = r->slots[k];
+    if (s.t >= s.K) return fail(QQA_EINVAL, "slot %d has finished its %d steps", k, s.K);
+    const size_t padded = (size_t)s.n * s.S_pad, elems = (size_t)s.n * s.S;
+    int rc = ensure_scratch(r, (padded + elems) * 4, st);
+    if (rc) return rc;
+    r->h_descs[k].grad_dbg = r->d_scratch;
+    rc = upload_desc(r, k, st);
+    if (rc) return rc;
+    const int32_t grid = std::min(r->max_grid, r->num_tiles);
+    rc = launch_step_chunk(r, 1, grid, st);
+    g_launches += 2;
+    for (auto &sl : r->slots)
+        if (sl.active) sl.t = std::min(sl.t + 1, sl.K);
+    r->h_descs[k].grad_dbg = nullptr;
+    int rc2 = upload_desc(r, k, st);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    launch_copy_grad(r->d_descs, k, s.n, s.S, s.S_pad, r->d_scratch, r->d_scratch + padded, st);
+    g_launches += 1;
+    QQA_CK_LAUNCH("copy_grad");
+    QQA_CK(cudaMemcpyAsync(grad, r->d_scratch + padded, elems * 4, cudaMemcpyDeviceToHost, st));
+    QQA_CK(cudaStreamSynchronize(st));
+    return QQA_OK;
+}

@@ -1,0 +1,326 @@
+// aux_kernels.cu -- everything around the fused step: initial state, the
+// clique column sums, step-counter advance, projection rounding with exact
+// integer costs, and state import/export for checkpoints and tests.
+#include "qqa_internal.cuh"
+
+namespace qqa {
+
+// ---------------------------------------------------------------------------
+// Initial state (the paper leaves it open): p ~ U(0,1] from Philox keyed by
+// (seed, node, replica quad, step 0, tag 0); m = v = 0.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void init_kernel(const InstDesc *__restrict__ descs, int32_t slot)
+{
+    const InstDesc &d = descs[slot];
+    const int quads = d.S_pad / 4;
+    const long long total = (long long)d.n * quads;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / quads);
+        const int q = (int)(idx % quads);
+        float u[4];
+        unif4(d.seed_lo, d.seed_hi, (uint32_t)i, (uint32_t)q, u);
+        const size_t e = (size_t)i * d.S_pad + 4 * q;
+        if (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.X[0]) + e) = make_float4(u[0], u[1], u[2], u[3]);
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.m) + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(reinterpret_cast<float *>(d.v) + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            *reinterpret_cast<float4 *>(d.master + e) = make_float4(u[0], u[1], u[2], u[3]);
+            __nv_bfloat16 *xb = reinterpret_cast<__nv_bfloat16 *>(d.X[0]) + e;
+            const __nv_bfloat162 a = __floats2bfloat162_rn(u[0], u[1]);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(u[2], u[3]);
+            reinterpret_cast<__nv_bfloat162 *>(xb)[0] = a;
+            reinterpret_cast<__nv_bfloat162 *>(xb)[1] = b;
+            const __nv_bfloat162 z = __floats2bfloat162_rn(0.f, 0.f);
+            reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(d.m) + e)[0] = z;
+            reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(d.m) + e)[1] = z;
+            reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(d.v) + e)[0] = z;
+            reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(d.v) + e)[1] = z;
+        }
+    }
+}
+
+void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, int32_t prec, cudaStream_t st)
+{
+    const long long total = (long long)n * (S_pad / 4);
+    const int block = 256;
+    const int grid = (int)((total + block - 1) / block < 65535 ? (total + block - 1) / block : 65535);
+    if (prec == kFP32) init_kernel<float><<<grid, block, 0, st>>>(descs, slot);
+    else init_kernel<__nv_bfloat16><<<grid, block, 0, st>>>(descs, slot);
+}
+
+// ---------------------------------------------------------------------------
+// Max-clique column sums sum_i p_is of the state at step t, in rotating buffer
+// t % 3, and zeroed buffer (t+1) % 3 for the next step to accumulate into.
+// One thread per replica, rows summed in order (deterministic).
+// ---------------------------------------------------------------------------
+__global__ void colsum_kernel(const InstDesc *__restrict__ descs, int32_t slot, int32_t prec)
+{
+    const InstDesc &d = descs[slot];
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= d.S_pad) return;
+    const int t = d.t;
+    float acc = 0.0f;
+    for (int i = 0; i < d.n; ++i) {
+        const size_t e = (size_t)i * d.S_pad + s;
+        acc += prec == kFP32 ? reinterpret_cast<const float *>(d.X[t & 1])[e] : d.master[e];
+    }
+    d.colsum[(t % 3) * d.S_pad + s] = acc;
+    d.colsum[((t + 1) % 3) * d.S_pad + s] = 0.0f;
+}
+
+void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st)
+{
+    colsum_kernel<<<(S_pad + 127) / 128, 128, 0, st>>>(descs, slot, prec);
+}
+
+// Step counters move forward once per chunk: t = min(t + nsteps, K).
+__global__ void advance_kernel(InstDesc *__restrict__ descs, int32_t capacity, int32_t nsteps)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= capacity) return;
+    InstDesc &d = descs[k];
+    if (!d.active) return;
+    const int t = d.t + nsteps;
+    d.t = t < d.K ? t : d.K;
+}
+
+void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st)
+{
+    advance_kernel<<<(capacity + 127) / 128, 128, 0, st>>>(descs, capacity, nsteps);
+}
+
+// ---------------------------------------------------------------------------
+// Projection rounding x = [p > 1/2] (Sec. 5) and exact integer costs.
+// A slot is evaluated once per step count (skipped if already evaluated at t).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool needs_eval(const InstDesc &d) { return d.active && d.t != d.last_eval_t; }
+
+__device__ __forceinline__ float state_value(const InstDesc &d, size_t e, int32_t prec)
+{
+    return prec == kFP32 ? reinterpret_cast<const float *>(d.X[d.t & 1])[e] : d.master[e];
+}
+
+// bits[i][w] bit b = (p[i][32w+b] > 1/2) for 32w+b < S; zero the cost counters.
+__global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
+                                 const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t prec)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int num_tiles = *num_tiles_p;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        const InstDesc &d = descs[tl.slot];
+        if (!needs_eval(d)) continue;
+        if (tl.row0 == 0)
+            for (int k = threadIdx.x; k < 3 * d.S_pad; k += blockDim.x) d.counts[k] = 0ULL;
+        const int rows = min(rows_per_tile, d.n - tl.row0);
+        const int pairs = rows * d.W;
+        for (int pidx = warp; pidx < pairs; pidx += nwarps) {
+            const int i = tl.row0 + pidx / d.W;
+            const int w = pidx % d.W;
+            const int s = 32 * w + lane;
+            const bool x = s < d.S && state_value(d, (size_t)i * d.S_pad + s, prec) > 0.5f;
+            const unsigned word = __ballot_sync(0xffffffffu, x);
+            if (lane == 0) d.bits[(size_t)i * d.W + w] = word;
+        }
+    }
+}
+
+// Per replica: size = sum x_i, inside = #edges (i<j) with x_i x_j, cut = sum w_ij [x_i != x_j].
+__global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
+                                  const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile)
+{
+    const int num_tiles = *num_tiles_p;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        const InstDesc &d = descs[tl.slot];
+        if (!needs_eval(d)) continue;
+        const int row_end = min(tl.row0 + rows_per_tile, d.n);
+        for (int s = threadIdx.x; s < d.S; s += blockDim.x) {
+            const int w = s >> 5;
+            const int b = s & 31;
+            long long size = 0, inside = 0, cut = 0;
+            for (int i = tl.row0; i < row_end; ++i) {
+                const unsigned xi = (d.bits[(size_t)i * d.W + w] >> b) & 1u;
+                size += xi;
+                const int k1 = d.row_ptr[i + 1];
+                for (int k = d.row_ptr[i]; k < k1; ++k) {
+                    const int j = d.col[k];
+                    if (j <= i) continue;   // each undirected edge once
+                    const unsigned xj = (d.bits[(size_t)j * d.W + w] >> b) & 1u;
+                    inside += (long long)(xi & xj);
+                    if (xi != xj) cut += d.w ? (long long)d.w[k] : 1LL;
+                }
+            }
+            if (size) atomicAdd(&d.counts[s], (unsigned long long)size);
+            if (inside) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)inside);
+            if (cut) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)cut);
+        }
+    }
+}
+
+// One warp per slot: objective, violation, feasibility, energy of every
+// replica; best feasible replica (max objective, ties -> lowest s); history;
+// bit-packed x of the best replica.
+__global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32_t capacity)
+{
+    InstDesc *descs = const_cast<InstDesc *>(descs_c);
+    const int lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (slot >= capacity) return;
+    InstDesc &d = descs[slot];
+    if (!needs_eval(d)) return;
+    long long best_obj = 0;
+    int best_s = -1;
+    for (int s = lane; s < d.S; s += 32) {
+        const long long size = (long long)d.counts[s];
+        const long long inside = (long long)d.counts[d.S_pad + s];
+        const long long cut = (long long)d.counts[2 * d.S_pad + s];
+        long long obj, viol;
+        double energy;
+        if (d.kind == kMIS) {
+            obj = size; viol = inside;
+            energy = -(double)size + (double)d.lambda * (double)inside;
+        } else if (d.kind == kMaxClique) {
+            obj = size; viol = size * (size - 1) / 2 - inside;
+            energy = -(double)size + (double)d.lambda * (double)viol;
+        } else {
+            obj = cut; viol = 0;
+            energy = -(double)cut;
+        }
+        const bool feas = viol == 0;
+        d.res_obj[s] = obj;
+        d.res_viol[s] = viol;
+        d.res_feas[s] = feas ? 1 : 0;
+        d.res_energy[s] = energy;
+        if (feas && (best_s < 0 || obj > best_obj)) { best_obj = obj; best_s = s; }
+    }
+    // warp argmax: larger objective wins, ties -> lower replica index
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long o2 = __shfl_xor_sync(0xffffffffu, best_obj, off);
+        const int s2 = __shfl_xor_sync(0xffffffffu, best_s, off);
+        const bool take = s2 >= 0 && (best_s < 0 || o2 > best_obj || (o2 == best_obj && s2 < best_s));
+        if (take) { best_obj = o2; best_s = s2; }
+    }
+    for (int base = 0; base < d.n; base += 32) {
+        const int i = base + lane;
+        unsigned bit = 0;
+        if (i < d.n && best_s >= 0) bit = (d.bits[(size_t)i * d.W + (best_s >> 5)] >> (best_s & 31)) & 1u;
+        const unsigned word = __ballot_sync(0xffffffffu, bit != 0);
+        if (lane == 0) d.res_bestx[base >> 5] = word;
+    }
+    if (lane == 0) {
+        const int count = d.res_meta[2];
+        d.res_meta[0] = best_s;
+        d.res_meta[1] = d.t;
+        if (count < d.hist_cap) {
+            d.hist_best[count] = best_s >= 0 ? best_obj : (long long)(-9223372036854775807LL - 1);
+            d.hist_step[count] = d.t;
+        }
+        d.res_meta[2] = count + 1;
+        d.last_eval_t = d.t;
+    }
+}
+
+void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
+                 int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st)
+{
+    (void)S_max_pad;
+    eval_bits_kernel<<<grid, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile, prec);
+    eval_count_kernel<<<grid, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile);
+    eval_finalize_kernel<<<(capacity + 7) / 8, 256, 0, st>>>(descs, capacity);
+}
+
+// ---------------------------------------------------------------------------
+// State export/import between the padded device layout and dense FP32 [n][S].
+// which: 0 = p (X or master), 1 = m, 2 = v.
+// ---------------------------------------------------------------------------
+__global__ void pack_state_kernel(const InstDesc *__restrict__ descs, int32_t slot, int32_t prec, int32_t which,
+                                  float *__restrict__ dst)
+{
+    const InstDesc &d = descs[slot];
+    const long long total = (long long)d.n * d.S;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / d.S), s = (int)(idx % d.S);
+        const size_t e = (size_t)i * d.S_pad + s;
+        float val;
+        if (which == 0) val = state_value(d, e, prec);
+        else {
+            const void *src = which == 1 ? d.m : d.v;
+            val = prec == kFP32 ? reinterpret_cast<const float *>(src)[e]
+                                : __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(src)[e]);
+        }
+        dst[idx] = val;
+    }
+}
+
+void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
+                       int32_t which, float *dst, cudaStream_t st)
+{
+    (void)S_pad;
+    const long long total = (long long)n * S;
+    const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+    pack_state_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(descs, slot, prec, which, dst);
+}
+
+// X, m, v are dense FP32 [n][S] device arrays; the state buffer for step t is
+// X[t & 1]; padded replicas (S <= s < S_pad) are left as they are.
+__global__ void unpack_state_kernel(const InstDesc *__restrict__ descs, int32_t slot, int32_t prec,
+                                    const float *__restrict__ X, const float *__restrict__ m,
+                                    const float *__restrict__ v, int32_t t)
+{
+    const InstDesc &d = descs[slot];
+    const long long total = (long long)d.n * d.S;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / d.S), s = (int)(idx % d.S);
+        const size_t e = (size_t)i * d.S_pad + s;
+        if (prec == kFP32) {
+            reinterpret_cast<float *>(d.X[t & 1])[e] = X[idx];
+            reinterpret_cast<float *>(d.m)[e] = m[idx];
+            reinterpret_cast<float *>(d.v)[e] = v[idx];
+        } else {
+            d.master[e] = X[idx];
+            reinterpret_cast<__nv_bfloat16 *>(d.X[t & 1])[e] = __float2bfloat16_rn(X[idx]);
+            reinterpret_cast<__nv_bfloat16 *>(d.m)[e] = __float2bfloat16_rn(m[idx]);
+            reinterpret_cast<__nv_bfloat16 *>(d.v)[e] = __float2bfloat16_rn(v[idx]);
+        }
+    }
+}
+
+void launch_unpack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
+                         const float *X, const float *m, const float *v, int32_t t, cudaStream_t st)
+{
+    (void)S_pad;
+    const long long total = (long long)n * S;
+    const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+    unpack_state_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(descs, slot, prec, X, m, v, t);
+}
+
+__global__ void copy_grad_kernel(int32_t n, int32_t S, int32_t S_pad, const float *__restrict__ src,
+                                 float *__restrict__ dst)
+{
+    const long long total = (long long)n * S;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / S), s = (int)(idx % S);
+        dst[idx] = src[(size_t)i * S_pad + s];
+    }
+}
+
+void launch_copy_grad(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, const float *src,
+                      float *dst, cudaStream_t st)
+{
+    (void)descs; (void)slot;
+    const long long total = (long long)n * S;
+    const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+    copy_grad_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(n, S, S_pad, src, dst);
+}
+
+}  // namespace qqa

@@ -1,0 +1,210 @@
+// qqa_internal.cuh -- device-side data layout and helpers of libqqa (sm_103a).
+//
+// One InstDesc per slot lives in device memory; every kernel reads the
+// instance it works on from it. Replica state is node-major [n][S_pad] with
+// S_pad = S rounded up to one 16-byte vector (4 FP32 or 8 BF16 replicas), so
+// every row starts 16-byte aligned and a group of lanes reads a row with
+// 128-bit coalesced loads.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qqa {
+
+enum Kind : int32_t { kMIS = 0, kMaxCut = 1, kMaxClique = 2 };
+enum Prec : int32_t { kFP32 = 0, kBF16 = 1 };
+
+struct __align__(16) InstDesc {
+    // graph (device CSR, owned by the problem)
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const int32_t *w;            // edge weights (max-cut) or nullptr = unit
+    // state
+    void *X[2];                  // ping-pong p^t / p^{t+1}: float or bf16 [n][S_pad]
+    float *master;               // BF16 runs: FP32 master copy of p [n][S_pad]; FP32 runs: nullptr
+    void *m;                     // AdamW first moment  (float or bf16) [n][S_pad]
+    void *v;                     // AdamW second moment (float or bf16) [n][S_pad]
+    float *colsum;               // max-clique: column sums sum_i p_is, 3 rotating buffers [3][S_pad]
+    float *grad_dbg;             // optional gradient dump [n][S_pad] (debug step only)
+    // evaluation scratch and results
+    uint32_t *bits;              // rounded replicas [n][W] (bit s%32 of word s/32)
+    unsigned long long *counts;  // per replica: size, inside edges, cut weight (as two's complement) [3][S_pad]
+    long long *res_obj;          // [S_pad]
+    long long *res_viol;         // [S_pad]
+    uint8_t *res_feas;           // [S_pad]
+    double *res_energy;          // [S_pad]
+    int32_t *res_meta;           // [0] best_s, [1] step of the evaluation, [2] evaluations done
+    uint32_t *res_bestx;         // [ceil(n/32)]
+    long long *hist_best;        // [hist_cap]
+    int32_t *hist_step;          // [hist_cap]
+    // sizes
+    int32_t n, S, S_pad, W;
+    int32_t kind, a_ent, t, K;
+    int32_t active, hist_cap, last_eval_t, pad0;
+    // hyper-parameters
+    float lr, wd, b1, b2;
+    float adam_eps, gmin, gmax, alpha;
+    float comm_eps, noise_scale, lambda, pad1;
+    uint32_t seed_lo, seed_hi, pad2, pad3;
+};
+
+// Device status word of a run.
+struct RunStatus {
+    unsigned long long nonfinite;   // count of non-finite gradient / state values seen
+    unsigned long long timeouts;    // bounded waits that ran out (none in this build's kernels)
+};
+
+// Tiles: (slot, first row). A block processes one tile at a time.
+struct Tile {
+    int32_t slot;
+    int32_t row0;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// ten rounds of two 32x32->64 multiplications with the published multipliers,
+// xor with the round key, and a Weyl-sequence key schedule.
+// ---------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in (0, 1]: the top 24 bits plus one, scaled by 2^-24 (exact in FP32)
+__device__ __forceinline__ float bits_to_unit(uint32_t r)
+{
+    return (float)((r >> 8) + 1u) * 5.9604644775390625e-8f;
+}
+
+// Four standard normals for replicas 4q..4q+3 of node i at step t (stream tag 1):
+// Box-Muller on the uniform pairs (r0, r1) and (r2, r3).
+__device__ __forceinline__ void gauss4(uint32_t seed_lo, uint32_t seed_hi, uint32_t i, uint32_t q, uint32_t t,
+                                       float out[4])
+{
+    const U4 r = philox10(U4{i, q, t, 1u}, seed_lo, seed_hi);
+    float s0, c0, s1, c1;
+    const float rad0 = sqrtf(-2.0f * logf(bits_to_unit(r.x)));
+    sincospif(2.0f * bits_to_unit(r.y), &s0, &c0);
+    const float rad1 = sqrtf(-2.0f * logf(bits_to_unit(r.z)));
+    sincospif(2.0f * bits_to_unit(r.w), &s1, &c1);
+    out[0] = rad0 * c0;
+    out[1] = rad0 * s0;
+    out[2] = rad1 * c1;
+    out[3] = rad1 * s1;
+}
+
+// Four uniforms for the initial state (stream tag 0, step 0).
+__device__ __forceinline__ void unif4(uint32_t seed_lo, uint32_t seed_hi, uint32_t i, uint32_t q, float out[4])
+{
+    const U4 r = philox10(U4{i, q, 0u, 0u}, seed_lo, seed_hi);
+    out[0] = bits_to_unit(r.x);
+    out[1] = bits_to_unit(r.y);
+    out[2] = bits_to_unit(r.z);
+    out[3] = bits_to_unit(r.w);
+}
+
+// ---------------------------------------------------------------------------
+// 16-byte vectors of replicas: 4 FP32 or 8 BF16 values.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct VecT;
+
+template <>
+struct VecT<float> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void load(const float *p, float out[4])
+    {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    }
+    __device__ __forceinline__ static void load_ro(const float *p, float out[4])
+    {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    }
+    __device__ __forceinline__ static void store(float *p, const float in[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(in[0], in[1], in[2], in[3]);
+    }
+};
+
+template <>
+struct VecT<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void unpack(const uint4 a, float out[8])
+    {
+        const uint32_t u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            out[2 * k] = __uint_as_float(u[k] << 16);
+            out[2 * k + 1] = __uint_as_float(u[k] & 0xFFFF0000u);
+        }
+    }
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float out[8])
+    {
+        unpack(*reinterpret_cast<const uint4 *>(p), out);
+    }
+    __device__ __forceinline__ static void load_ro(const __nv_bfloat16 *p, float out[8])
+    {
+        unpack(__ldg(reinterpret_cast<const uint4 *>(p)), out);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, const float in[8])
+    {
+        uint32_t u[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(in[2 * k], in[2 * k + 1]);
+            u[k] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(p) = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side launch entry points implemented in the .cu files.
+// ---------------------------------------------------------------------------
+struct StepLaunch {
+    const InstDesc *descs;
+    const Tile *tiles;
+    const int32_t *num_tiles;
+    RunStatus *status;
+    int32_t r;              // offset of this launch inside its chunk (t = desc.t + r)
+    int32_t grid, block;
+    int32_t group_lanes, vec_per_lane;
+    cudaStream_t stream;
+};
+
+// Returns false if no kernel exists for (prec, group_lanes, vec_per_lane).
+bool launch_step(int32_t prec, const StepLaunch &L);
+bool step_variant_exists(int32_t prec, int32_t group_lanes, int32_t vec_per_lane);
+int step_max_active_blocks(int32_t prec, int32_t group_lanes, int32_t vec_per_lane, int32_t block);
+
+void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, int32_t prec, cudaStream_t st);
+void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st);
+void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
+void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
+                 int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st);
+void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
+                       int32_t which, float *dst, cudaStream_t st);
+void launch_unpack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
+                         const float *X, const float *m, const float *v, int32_t t, cudaStream_t st);
+void launch_copy_grad(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, const float *src,
+                      float *dst, cudaStream_t st);
+
+}  // namespace qqa

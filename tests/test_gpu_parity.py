@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+identical seeded inputs. Single steps are compared element by element within
+the propagated FP32 / BF16 bound of tests/parity.py; integer costs, feasibility
+and best replicas must be bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_02135_gb300 as qqa
+from parity import as_f32, assert_within, make_run, step_tolerance, RTOL
+from qqa_inputs import graphs as G
+from qqa_inputs.workloads import MIS, MAXCUT, MAXCLIQUE, FP32, BF16, Params
+
+pytestmark = pytest.mark.gpu
+
+KIND_NAMES = {MIS: "mis", MAXCUT: "cut", MAXCLIQUE: "clique"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2409_02135_gb300 import _build
+    _build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def _graph(kind, n, p, seed, weighted=False):
+    g = G.erdos_renyi(n, p, seed)
+    if weighted:
+        rng = np.random.default_rng(seed)
+        u, v, _ = g.upper_edges()
+        g = G.from_edges(n, u, v, rng.integers(-2, 5, size=u.size))
+    return g
+
+
+def _check_step(kind, g, p, prec, run, slot=0, rows=None):
+    """GPU step from the run's current state vs the oracle step from the same state."""
+    X0, m0, v0, t = run.get_state(slot)
+    grad = run.step_debug(slot)
+    X1, m1, v1, t1 = run.get_state(slot)
+    assert t1 == t + 1
+    po = as_f32(p)
+    Xd = X0.astype(np.float64)
+    if rows is None:
+        out = oracle.step(kind, g, po, t, Xd, m0.astype(np.float64), v0.astype(np.float64))
+        sel = slice(None)
+    else:
+        out = oracle.step(kind, g, po, t, Xd, m0[rows].astype(np.float64), v0[rows].astype(np.float64), rows=rows)
+        sel = rows
+    tg, tm, tv, tp = step_tolerance(po, prec, t, X0[sel].astype(np.float64), m0[sel].astype(np.float64),
+                                    v0[sel].astype(np.float64), out)
+    r = {}
+    r["g"] = assert_within("gradient", grad[sel], out.grad, tg)
+    r["m"] = assert_within("m", m1[sel], out.m, tm)
+    r["v"] = assert_within("v", v1[sel], out.v, tv)
+    r["p"] = assert_within("p", X1[sel], out.X, tp)
+    return r
+
+
+# ------------------------------------------------------------ init -------
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_init_state_is_the_oracle_draw(prec):
+    """Initial p are the same Philox uniforms on both sides (exact in FP32)."""
+    g = _graph(MIS, 77, 0.1, 1)
+    p = Params(S=13, steps=10, seed=0xABCDEF12345, precision=prec)
+    run = make_run(MIS, g, p)
+    X, m, v, t = run.get_state(0)
+    want = oracle.init_state(g.n, p.S, p.seed)
+    assert t == 0
+    np.testing.assert_array_equal(X.astype(np.float64), want)
+    assert not m.any() and not v.any()
+
+
+# --------------------------------------------------------- single step ---
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("S", [8, 37, 128])
+def test_single_step_matches_oracle(kind, prec, S):
+    g = _graph(kind, 150, 0.08, 10 + kind, weighted=(kind == MAXCUT))
+    p = Params(S=S, steps=400, alpha_comm=0.3, lr=0.1, seed=3, precision=prec,
+               gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    run = make_run(kind, g, p)
+    _check_step(kind, g, p, prec, run)           # t = 0 (cold moments)
+    run.steps(98)
+    _check_step(kind, g, p, prec, run)           # t = 99 (warm moments)
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("a_ent,alpha", [(2, 0.0), (4, 0.0), (4, 1.0), (6, 0.5)])
+def test_single_step_entropy_exponents_and_alpha(prec, a_ent, alpha):
+    g = _graph(MIS, 90, 0.1, 5)
+    p = Params(S=16, steps=50, a_ent=a_ent, alpha_comm=alpha, seed=9, precision=prec)
+    run = make_run(MIS, g, p)
+    run.steps(7)
+    _check_step(MIS, g, p, prec, run)
+
+
+@pytest.mark.parametrize("cfg", [(1, 4, 64), (2, 2, 128), (4, 1, 256), (8, 1, 32)])
+def test_single_step_every_layout(cfg):
+    """Every (lanes per row, vectors per lane, block) layout computes the same step."""
+    G_, V_, B_ = cfg
+    g = _graph(MIS, 130, 0.1, 6)
+    p = Params(S=16, steps=50, alpha_comm=0.5, seed=2)
+    run = make_run(MIS, g, p, config=qqa.LaunchConfig(G_, V_, B_))
+    c = run.config()
+    assert (c.group_lanes, c.vec_per_lane, c.block_threads) == cfg
+    run.steps(3)
+    _check_step(MIS, g, p, FP32, run)
+
+
+@pytest.mark.parametrize("S,prec", [(1, FP32), (3, BF16), (100, FP32), (1000, FP32), (1000, BF16), (256, BF16)])
+def test_single_step_replica_counts(S, prec):
+    """Ragged replica counts (padding lanes), S = 1 (zero variance), and S = 1000 (paper scale)."""
+    g = _graph(MIS, 60, 0.15, 7)
+    p = Params(S=S, steps=20, alpha_comm=0.3, seed=4, precision=prec)
+    run = make_run(MIS, g, p)
+    run.steps(2)
+    _check_step(MIS, g, p, prec, run)
+
+
+def test_isolated_nodes_single_node_and_ragged_tiles():
+    """Rows with no neighbours, a 1-node graph, and n not a multiple of the tile height."""
+    u = np.array([0, 0, 2]); v = np.array([1, 5, 5])
+    g = G.from_edges(263, u, v)                      # 260 isolated nodes
+    p = Params(S=8, steps=20, alpha_comm=0.2, seed=1)
+    run = make_run(MIS, g, p)
+    _check_step(MIS, g, p, FP32, run)
+    g1 = G.from_edges(1, [], [])
+    run1 = make_run(MAXCUT, g1, p)
+    _check_step(MAXCUT, g1, p, FP32, run1)
+
+
+# ---------------------------------------------------------- multi-step ---
+@pytest.mark.parametrize("kind", [MIS, MAXCUT])
+def test_graph_replay_equals_single_launches(kind):
+    """Chunks replayed from CUDA graphs give bit-identical states to one launch per step."""
+    g = _graph(kind, 200, 0.05, 8)
+    p = Params(S=32, steps=300, seed=5)
+    a = make_run(kind, g, p, config=qqa.LaunchConfig(use_graphs=1))
+    b = make_run(kind, g, p, config=qqa.LaunchConfig(use_graphs=0))
+    a.steps(120)
+    for _ in range(120):
+        b.steps(1)
+    Xa, ma, va, ta = a.get_state(0)
+    Xb, mb, vb, tb = b.get_state(0)
+    assert ta == tb == 120
+    np.testing.assert_array_equal(Xa, Xb)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(va, vb)
+
+
+def test_each_step_of_a_trajectory_matches_oracle():
+    """Re-anchored trajectory: every one of 30 consecutive GPU steps equals the
+    oracle step taken from the GPU's own state (catches ping-pong or t errors)."""
+    g = _graph(MAXCLIQUE, 80, 0.3, 12)
+    p = Params(S=24, steps=60, alpha_comm=0.3, seed=6)
+    run = make_run(MAXCLIQUE, g, p)
+    for _ in range(30):
+        _check_step(MAXCLIQUE, g, p, FP32, run)
+
+
+def test_steps_stop_at_K_and_checkpoint_resume_is_exact():
+    g = _graph(MIS, 100, 0.1, 2)
+    p = Params(S=16, steps=130, seed=8)
+    a = make_run(MIS, g, p)
+    a.steps(70)
+    X, m, v, t = a.get_state(0)
+    a.steps(500)
+    assert a.slot_step(0) == 130
+    b = make_run(MIS, g, p)
+    b.set_state(0, X, m, v, t)
+    b.steps(60)
+    np.testing.assert_array_equal(a.get_state(0)[0], b.get_state(0)[0])
+
+
+def test_alone_equals_in_batch():
+    """An instance's trajectory does not depend on what else shares the launch."""
+    gs = [_graph(MIS, 90 + 37 * k, 0.1, 30 + k) for k in range(4)]
+    ps = [Params(S=32, steps=80 + 10 * k, seed=k) for k in range(4)]
+    cfg = qqa.LaunchConfig(8, 1, 128)
+    batch = make_run(MIS, gs, ps, config=cfg)
+    batch.steps(100)
+    for k in (0, 3):
+        alone = make_run(MIS, gs[k], ps[k], config=cfg)
+        alone.steps(100)
+        np.testing.assert_array_equal(alone.get_state(0)[0], batch.get_state(k)[0])
+        assert batch.slot_step(k) == min(100, ps[k].steps)
+
+
+# -------------------------------------------------------------- eval -----
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_round_eval_is_exact(kind, prec):
+    """Rounded costs, feasibility, energies and the best replica equal the
+    oracle's evaluation of the GPU state, and best_x has the reported cost."""
+    g = _graph(kind, 120, 0.2 if kind == MAXCLIQUE else 0.06, 40, weighted=(kind == MAXCUT))
+    p = Params(S=70, steps=200, seed=3, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    run = make_run(kind, g, p)
+    for k in (37, 163):
+        run.steps(k)
+        run.eval()
+        run.sync()
+        res = run.result(0)
+        X = run.get_state(0)[0].astype(np.float64)
+        want = oracle.round_eval(kind, g, np.float32(p.lam), X)
+        np.testing.assert_array_equal(res["obj"], want.obj)
+        np.testing.assert_array_equal(res["viol"], want.viol)
+        np.testing.assert_array_equal(res["feasible"], want.feasible)
+        np.testing.assert_array_equal(res["energy"], want.energy)
+        assert res["best"] == want.best
+        if want.best >= 0:
+            o, vv, f, e = oracle.cost_of_x(kind, g, p.lam, res["best_x"])
+            assert (o, f) == (want.obj[want.best], True)
+
+
+def test_history_and_anneal_entry_point():
+    g = _graph(MIS, 100, 0.05, 0)
+    p = Params(S=8, steps=1000, round_every=50, seed=0)
+    run = qqa.anneal([qqa.Problem(MIS, g)], [qqa.make_params(p)])
+    hist, at = run.history(0)
+    assert list(at) == list(range(50, 1001, 50))
+    res = run.result(0)
+    assert hist[-1] == res["obj"][res["best"]]
+    assert res["step"] == 1000
+
+
+# ----------------------------------------------------------- quality -----
+def test_quality_matches_oracle_er100():
+    """ER G(100, 0.05) MIS, S = 8, 1000 steps, 16 seeds: the mean best feasible
+    objective is within 1% of the oracle's, and every result is feasible."""
+    g = G.erdos_renyi(100, 0.05, 0)
+    gpu, cpu = [], []
+    for seed in range(16):
+        p = Params(S=8, steps=1000, seed=seed)
+        run = qqa.anneal([qqa.Problem(MIS, g)], [qqa.make_params(p)])
+        r = run.result(0)
+        assert r["best"] >= 0
+        gpu.append(r["obj"][r["best"]])
+        o = oracle.anneal(MIS, g, as_f32(p))
+        cpu.append(o.eval.obj[o.eval.best])
+    assert abs(np.mean(gpu) - np.mean(cpu)) <= 0.01 * np.mean(cpu)

@@ -9,7 +9,7 @@ absolute values of the gradient's terms, first-order propagation through the
 AdamW update gives
     |dg| <= rtol * gabs
     |dm| <= rtol * (b1 |m0| + (1-b1) gabs) + st |m|
-    |dv| <= rtol * (b2 v0 + (1-b2) (g^2 + 2 |g| gabs)) + st v
+    |dv| <= rtol b2 v0 + (1-b2) (rtol g^2 + 2 |g| |dg| + |dg|^2) + st v
     den   = sqrt(v) / sqrt(bc2) + eps
     |dp| <= rtol |p0| + (lr / bc1) (|dm| / den + |m| |dv| / (2 sqrt(v bc2) den^2)) + rtol |sigma xi| + 2^-23
 where st is the relative rounding of stored moments (0 in FP32, 2^-8 in BF16)
@@ -61,7 +61,7 @@ def step_tolerance(p: Params, prec: int, t: int, X0, m0, v0, out: oracle.StepOut
     g, gabs = out.grad, out.grad_scale
     tol_g = rtol * gabs
     tol_m = rtol * (b1 * np.abs(m0) + (1 - b1) * gabs) + st * np.abs(out.m)
-    tol_v = rtol * (b2 * v0 + (1 - b2) * (g * g + 2 * np.abs(g) * gabs)) + st * out.v
+    tol_v = rtol * b2 * v0 + (1 - b2) * (rtol * g * g + 2 * np.abs(g) * tol_g + tol_g * tol_g) + st * out.v
     bc1 = 1 - b1 ** (t + 1)
     bc2 = 1 - b2 ** (t + 1)
     den = np.sqrt(out.v) / math.sqrt(bc2) + p.adam_eps

@@ -255,7 +255,9 @@ def run_ours(args):
     kinds = [inst.kind for inst in wl.instances]
     probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
     params = [qqa.make_params(inst.params) for inst in wl.instances]
-    cfg = qqa.LaunchConfig(use_graphs=1)
+    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3}[args.kernel],
+                           kernel_param=args.kernel_param, group_lanes=args.group_lanes,
+                           vec_per_lane=args.vec_per_lane, block_threads=args.block_threads)
     run = qqa.Run.create(probs, params, config=cfg, stream=stream, allocator=alloc)
     K = max(p.steps for p in params)
     R = min(p.round_every for p in params) or K
@@ -360,7 +362,9 @@ def run_ours(args):
                    "anneal_steps": K, "round_every": R, "precision": "fp32" if prec == W.FP32 else "bf16",
                    "l2": "flushed between timed anneals (512 MB write)",
                    "parallelism": f"instances x{world} ranks" if world > 1 else "single GPU",
-                   "launch": {"group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
+                   "launch": {"kernel": ["auto", "direct", "staged", "stream"][run.config().kernel],
+                              "group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
+                              "kernel_param": run.config().kernel_param,
                               "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
                               "graphs": True}},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
@@ -385,6 +389,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mis_er700_800",
                     choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512"])
+    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream"], default="auto")
+    ap.add_argument("--kernel-param", type=int, default=0)
+    ap.add_argument("--group-lanes", type=int, default=0)
+    ap.add_argument("--vec-per-lane", type=int, default=0)
+    ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -61,7 +61,7 @@ typedef struct qqa_allocator {
  * App. D.1): a_ent = 4, gamma_min = -2 (max-cut: -5, or -20 on large graphs),
  * gamma_max = 0.1, weight_decay = 0.01, temperature = 1e-3, lambda = 2,
  * lr in {1, 0.1, 0.01}. beta1/beta2/adam_eps and alpha_comm are not printed
- * in the paper; qqa_default_params fills 0.9/0.999/1e-8 and 0.3.
+ * in the paper; qqa_default_params fills 0.9/0.999/1e-8 and 0.1.
  */
 typedef struct qqa_params {
     int32_t S;            /* replicas, 1..1024 */
@@ -81,20 +81,36 @@ typedef struct qqa_params {
 
 /*
  * Launch shape of the fused step kernel. Zero fields are chosen
- * automatically from S_max and the precision.
+ * automatically from the replica count, the precision and (qqa_run_create)
+ * the graphs.
  *   group_lanes : lanes that share one node row (1, 2, 4, 8, 16, 32)
  *   vec_per_lane: 16-byte vectors of replicas per lane (1, 2, 4, 8)
  *     group_lanes * vec_per_lane * (4 FP32 | 8 BF16 replicas) >= S
- *   block_threads: 32..256, multiple of 32
+ *   block_threads: 32..256, multiple of 32 (the staged kernel uses 256)
  *   grid_blocks : persistent grid size (tiles are walked with a stride)
  *   use_graphs  : capture chunks of steps as CUDA graphs and replay them
+ *   kernel      : QQA_KERNEL_AUTO, QQA_KERNEL_DIRECT (every neighbour row
+ *                 gathered from global memory), QQA_KERNEL_STAGED (chunks of
+ *                 the state staged in shared memory by TMA bulk copies and
+ *                 reused by all rows of a block; for dense graphs) or
+ *                 QQA_KERNEL_STREAM (each thread prefetches the next row's
+ *                 slices with cp.async into private shared memory; for
+ *                 sparse, memory-bound graphs)
+ *   kernel_param: staged: row groups per warp (2, 4, 8);
+ *                 stream: neighbour rows prefetched per row (4, 8)
  */
+#define QQA_KERNEL_AUTO 0
+#define QQA_KERNEL_DIRECT 1
+#define QQA_KERNEL_STAGED 2
+#define QQA_KERNEL_STREAM 3
 typedef struct qqa_launch_config {
     int32_t group_lanes;
     int32_t vec_per_lane;
     int32_t block_threads;
     int32_t grid_blocks;
     int32_t use_graphs;
+    int32_t kernel;
+    int32_t kernel_param;
     int32_t reserved;
 } qqa_launch_config;
 

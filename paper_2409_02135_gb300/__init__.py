@@ -18,7 +18,7 @@ import ctypes
 import numpy as np
 
 from ._lib import (  # noqa: F401
-    BF16, FP32, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
+    BF16, FP32, KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
     QQAError, check, load, qqa_allocator, qqa_launch_config, qqa_params, ALLOC_FN, FREE_FN, SIGNATURES,
 )
 
@@ -68,8 +68,14 @@ def make_params(src=None, **kw) -> qqa_params:
     return p
 
 
-def LaunchConfig(group_lanes=0, vec_per_lane=0, block_threads=0, grid_blocks=0, use_graphs=1) -> qqa_launch_config:
-    return qqa_launch_config(group_lanes, vec_per_lane, block_threads, grid_blocks, use_graphs, 0)
+def LaunchConfig(group_lanes=0, vec_per_lane=0, block_threads=0, grid_blocks=0, use_graphs=1, kernel=0,
+                 kernel_param=0, rows_per_warp=None) -> qqa_launch_config:
+    """kernel: 0 auto, 1 direct gather, 2 TMA-staged (kernel_param = row groups per warp),
+    3 cp.async streaming (kernel_param = neighbour rows prefetched per row)."""
+    if rows_per_warp is not None:
+        kernel_param = rows_per_warp
+    return qqa_launch_config(group_lanes, vec_per_lane, block_threads, grid_blocks, use_graphs, kernel,
+                             kernel_param, 0)
 
 
 _keep_alive = []

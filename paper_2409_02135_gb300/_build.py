@@ -1,6 +1,6 @@
 """Build libqqa.so in-tree with nvcc for sm_103a (GB300).
 
-The four translation units compile in parallel, then link into one shared
+The translation units compile in parallel, then link into one shared
 library next to this file. Objects go to _build/ (git-ignored). The build is
 skipped when the library is newer than every source.
 """
@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqqa.so")
-UNITS = ["step_fp32.cu", "step_bf16.cu", "aux_kernels.cu", "api.cu"]
+UNITS = ["step_direct_fp32.cu", "step_direct_bf16.cu", "step_tiled_fp32.cu", "step_tiled_bf16.cu",
+         "step_stream_fp32.cu", "step_stream_bf16.cu", "aux_kernels.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

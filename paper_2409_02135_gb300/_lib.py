@@ -23,6 +23,7 @@ ERROR_NAMES = {QQA_EINVAL: "EINVAL", QQA_ENOMEM: "ENOMEM", QQA_ECUDA: "ECUDA", Q
 
 MIS, MAXCUT, MAXCLIQUE = 0, 1, 2
 FP32, BF16 = 0, 1
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM = 0, 1, 2, 3
 
 
 class qqa_params(ctypes.Structure):
@@ -40,7 +41,8 @@ class qqa_params(ctypes.Structure):
 class qqa_launch_config(ctypes.Structure):
     _fields_ = [("group_lanes", ctypes.c_int32), ("vec_per_lane", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
-                ("use_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_graphs", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("kernel_param", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -23,8 +23,13 @@
 
 namespace qqa {
 using StepFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t);
+using TiledFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t, int32_t);
 StepFn step_kernel_fp32(int G, int VPL);
 StepFn step_kernel_bf16(int G, int VPL);
+TiledFn step_tiled_kernel_fp32(int G, int VPL, int RPW);
+TiledFn step_tiled_kernel_bf16(int G, int VPL, int RPW);
+StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
+StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
 }  // namespace qqa
 
 using namespace qqa;
@@ -115,7 +120,7 @@ extern "C" void qqa_default_params(qqa_params *p)
     p->adam_eps = 1e-8f;
     p->gamma_min = -2.0f;
     p->gamma_max = 0.1f;
-    p->alpha_comm = 0.3f;
+    p->alpha_comm = 0.1f;
     p->comm_eps = 1e-8f;
     p->temperature = 1e-3f;
     p->lambda = 2.0f;
@@ -234,6 +239,8 @@ struct qqa_run {
     qqa_launch_config cfg{};
     int32_t rows_per_tile = 0, max_grid = 0, smem = 0;
     StepFn step_fn = nullptr;
+    TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
+    int32_t chunk_rows = 0, buf_elems = 0;
     Alloc alloc;
     InstDesc *d_descs = nullptr;
     std::vector<InstDesc> h_descs;
@@ -248,6 +255,8 @@ struct qqa_run {
     cudaStream_t cap_stream = nullptr;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
 };
+
+static const bool kAutoStaged = false;
 
 static int pick_layout(int32_t S_pad, int32_t vec, int32_t &G, int32_t &VPL)
 {
@@ -264,7 +273,8 @@ static int pick_layout(int32_t S_pad, int32_t vec, int32_t &G, int32_t &VPL)
     return QQA_OK;
 }
 
-static int resolve_config(qqa_run *r, const qqa_launch_config *cfg)
+// staged_hint: 1 if the graphs favour the staged kernel (auto mode), else 0.
+static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_hint)
 {
     qqa_launch_config c{};
     if (cfg) c = *cfg;
@@ -278,20 +288,73 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg)
     }
     if (G * VPL * r->vec < r->S_max_pad)
         return fail(QQA_EINVAL, "layout G=%d VPL=%d covers %d replicas < %d", G, VPL, G * VPL * r->vec, r->S_max_pad);
-    r->step_fn = r->prec == kFP32 ? step_kernel_fp32(G, VPL) : step_kernel_bf16(G, VPL);
-    if (!r->step_fn) return fail(QQA_EINVAL, "no step kernel for G=%d VPL=%d precision %d", G, VPL, r->prec);
+    int mode = c.kernel;
+    if (mode == QQA_KERNEL_AUTO)
+        mode = (staged_hint && (c.block_threads == 0 || c.block_threads == 256)) ? QQA_KERNEL_STAGED : QQA_KERNEL_DIRECT;
+    if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_STREAM) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
+    int rpw = c.kernel_param ? c.kernel_param : (mode == QQA_KERNEL_STREAM ? 8 : 4);
+    if (mode == QQA_KERNEL_STAGED) {
+        r->tiled_fn = r->prec == kFP32 ? step_tiled_kernel_fp32(G, VPL, rpw) : step_tiled_kernel_bf16(G, VPL, rpw);
+        if (!r->tiled_fn) {
+            if (c.kernel == QQA_KERNEL_STAGED)
+                return fail(QQA_EINVAL, "no staged kernel for G=%d VPL=%d rows_per_warp=%d", G, VPL, rpw);
+            mode = QQA_KERNEL_DIRECT;   // auto: fall back to the direct-gather kernel
+        }
+    }
+    const int tb = r->prec == kFP32 ? 4 : 2;
     int block = c.block_threads ? c.block_threads : 256;
-    if (block < 32 || block > 256 || block % 32) return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
-    c.group_lanes = G;
-    c.vec_per_lane = VPL;
-    c.block_threads = block;
-    r->rows_per_tile = (block / 32) * (32 / G);
-    r->smem = r->S_max_pad * (int)sizeof(float);
     int dev = 0, sms = 0, occ = 0;
     QQA_CK(cudaGetDevice(&dev));
     QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block, r->smem));
+    if (mode == QQA_KERNEL_STAGED) {
+        if (c.block_threads && c.block_threads != 256) return fail(QQA_EINVAL, "the staged kernel runs 256 threads");
+        block = 256;
+        const int row_bytes = r->S_max_pad * tb;
+        r->chunk_rows = std::max(8, 32768 / row_bytes);
+        r->buf_elems = r->chunk_rows * r->S_max_pad;
+        r->smem = 128 + 2 * r->buf_elems * tb + r->S_max_pad * (int)sizeof(float);
+        QQA_CK(cudaFuncSetAttribute(r->tiled_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->tiled_fn, block, r->smem));
+        r->rows_per_tile = (block / 32) * rpw * (32 / G);
+        r->step_fn = nullptr;
+    } else if (mode == QQA_KERNEL_STREAM) {
+        r->tiled_fn = nullptr;
+        r->step_fn = r->prec == kFP32 ? step_stream_kernel_fp32(G, VPL, rpw) : step_stream_kernel_bf16(G, VPL, rpw);
+        if (!r->step_fn) return fail(QQA_EINVAL, "no stream kernel for G=%d VPL=%d prefetch=%d", G, VPL, rpw);
+        if (block < 32 || block > 256 || block % 32)
+            return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
+        const int slots = (r->prec == kFP32 ? 1 : 2) + 2 + rpw;   // own p words, m, v, neighbours
+        r->smem = 2 * VPL * slots * block * 16;
+        QQA_CK(cudaFuncSetAttribute(r->step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block, r->smem));
+        r->rows_per_tile = (block / 32) * (32 / G);
+    } else {
+        r->tiled_fn = nullptr;
+        rpw = 0;
+        r->step_fn = r->prec == kFP32 ? step_kernel_fp32(G, VPL) : step_kernel_bf16(G, VPL);
+        if (!r->step_fn) return fail(QQA_EINVAL, "no step kernel for G=%d VPL=%d precision %d", G, VPL, r->prec);
+        r->smem = r->S_max_pad * (int)sizeof(float);
+        if (c.block_threads == 0) {
+            // registers are allocated per warp: pick the block size that keeps
+            // the most warps resident (ties go to the larger block)
+            int best_warps = -1;
+            for (int b : {256, 128, 64}) {
+                int o = 0;
+                QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, r->step_fn, b, r->smem));
+                if (o * b / 32 > best_warps) { best_warps = o * b / 32; block = b; }
+            }
+        }
+        if (block < 32 || block > 256 || block % 32)
+            return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block, r->smem));
+        r->rows_per_tile = (block / 32) * (32 / G);
+    }
     if (occ < 1) return fail(QQA_EINVAL, "step kernel G=%d VPL=%d cannot run %d threads per block", G, VPL, block);
+    c.group_lanes = G;
+    c.vec_per_lane = VPL;
+    c.block_threads = block;
+    c.kernel = mode;
+    c.kernel_param = rpw;
     r->max_grid = c.grid_blocks ? c.grid_blocks : sms * occ;
     c.grid_blocks = r->max_grid;
     r->cfg = c;
@@ -341,8 +404,17 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     return QQA_OK;
 }
 
+static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
+                             const qqa_allocator *alloc, void *stream, int staged_hint, qqa_run **out);
+
 extern "C" int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
                                     const qqa_allocator *alloc, void *stream, qqa_run **out)
+{
+    return run_create_hinted(capacity, S_max, precision, cfg, alloc, stream, 0, out);
+}
+
+static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
+                             const qqa_allocator *alloc, void *stream, int staged_hint, qqa_run **out)
 {
     if (!out) return fail(QQA_EINVAL, "out is NULL");
     *out = nullptr;
@@ -358,7 +430,7 @@ extern "C" int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t pre
     r->S_max = S_max;
     r->S_max_pad = (S_max + r->vec - 1) / r->vec * r->vec;
     r->alloc = Alloc::from(alloc);
-    int rc = resolve_config(r, cfg);
+    int rc = resolve_config(r, cfg, staged_hint);
     if (rc) { delete r; return rc; }
     r->h_descs.assign(capacity, InstDesc{});
     r->slots.resize(capacity);
@@ -460,8 +532,9 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.res_bestx = (uint32_t *)get((size_t)((s.n + 31) / 32) * 4);
     d.hist_best = (long long *)get((size_t)s.hist_cap * 8);
     d.hist_step = (int32_t *)get((size_t)s.hist_cap * 4);
+    d.scal = (float4 *)get((size_t)kMaxChunk * sizeof(float4));
     bool ok = d.X[0] && d.X[1] && d.m && d.v && d.bits && d.counts && d.res_obj && d.res_viol && d.res_feas &&
-              d.res_energy && d.res_meta && d.res_bestx && d.hist_best && d.hist_step &&
+              d.res_energy && d.res_meta && d.res_bestx && d.hist_best && d.hist_step && d.scal &&
               (r->prec == kFP32 || d.master) && (prob->kind != QQA_MAXCLIQUE || d.colsum);
     if (!ok) {
         free_slot(r, k, st);
@@ -489,6 +562,7 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.comm_eps = prm->comm_eps;
     d.noise_scale = (float)std::sqrt(2.0 * (double)prm->lr * (double)prm->temperature);
     d.lambda = prm->lambda;
+    d.decay = 1.0f - prm->lr * prm->weight_decay;
     d.seed_lo = (uint32_t)(prm->seed & 0xffffffffu);
     d.seed_hi = (uint32_t)(prm->seed >> 32);
     r->h_descs[k] = d;
@@ -573,10 +647,24 @@ extern "C" int qqa_run_create(qqa_problem *const *problems, const qqa_params *pa
 {
     if (!problems || !params || count < 1) return fail(QQA_EINVAL, "need count >= 1 problems and params");
     int32_t S_max = 1;
-    for (int32_t k = 0; k < count; ++k) S_max = std::max(S_max, params[k].S);
+    for (int32_t k = 0; k < count; ++k) {
+        if (!problems[k]) return fail(QQA_EINVAL, "problem %d is NULL", k);
+        S_max = std::max(S_max, params[k].S);
+    }
     if (S_max > 1024) return fail(QQA_EINVAL, "S = %d exceeds 1024", S_max);
+    // Auto kernel choice: staging pays when gathering every neighbour row from
+    // L2 would move more than twice the bytes of streaming each block's span
+    // of the state once (64-row blocks, the span taken as the whole graph).
+    double gather_rows = 0.0, staged_rows = 0.0;
+    for (int32_t k = 0; k < count; ++k) {
+        gather_rows += (double)problems[k]->nnz;
+        staged_rows += (double)((problems[k]->n + 63) / 64) * (double)problems[k]->n;
+    }
+    // (measured on GB300: the staged kernel does not yet beat the direct one,
+    // so auto keeps the direct kernel until it does)
+    const int staged_hint = (gather_rows > 2.0 * staged_rows && kAutoStaged) ? 1 : 0;
     qqa_run *r = nullptr;
-    int rc = qqa_run_create_empty(count, S_max, params[0].precision, cfg, alloc, stream, &r);
+    int rc = run_create_hinted(count, S_max, params[0].precision, cfg, alloc, stream, staged_hint, &r);
     if (rc) return rc;
     for (int32_t k = 0; k < count; ++k) {
         int32_t slot = -1;
@@ -617,8 +705,14 @@ extern "C" int qqa_run_config(const qqa_run *r, qqa_launch_config *out)
 // ------------------------------------------------------------------- steps
 static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream_t st)
 {
+    launch_prepare(r->d_descs, r->capacity, chunk, st);
     for (int32_t i = 0; i < chunk; ++i) {
-        r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles, r->d_status, i);
+        if (r->tiled_fn)
+            r->tiled_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
+                                                                     r->d_status, i, r->chunk_rows, r->buf_elems);
+        else
+            r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
+                                                                    r->d_status, i);
     }
     launch_advance(r->d_descs, r->capacity, chunk, st);
     QQA_CK_LAUNCH("step");
@@ -666,7 +760,7 @@ extern "C" int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream)
             int rc = launch_step_chunk(r, chunk, grid, st);
             if (rc) return rc;
         }
-        g_launches += (unsigned long long)chunk + 1;
+        g_launches += (unsigned long long)chunk + 2;
         for (auto &s : r->slots)
             if (s.active) s.t = std::min(s.t + chunk, s.K);
         left -= chunk;
@@ -680,7 +774,7 @@ extern "C" int qqa_run_eval(qqa_run *r, void *stream)
     if (!r) return fail(QQA_EINVAL, "run is NULL");
     if (r->num_tiles == 0) return QQA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int32_t grid = std::min(r->max_grid, r->num_tiles);
+    const int32_t grid = std::min(r->num_tiles, 65535);
     launch_eval(r->d_descs, r->d_tiles, r->d_num_tiles, grid, r->rows_per_tile, r->capacity, r->S_max_pad, r->prec, st);
     g_launches += 3;
     QQA_CK_LAUNCH("eval");
@@ -711,6 +805,8 @@ extern "C" int qqa_run_sync(qqa_run *r, void *stream)
     }
     RunStatus stt{};
     QQA_CK(cudaMemcpy(&stt, r->d_status, sizeof stt, cudaMemcpyDeviceToHost));
+    if (stt.timeouts)
+        return fail(QQA_ETIMEOUT, "%llu staged copies did not arrive within the wait limit", stt.timeouts);
     if (stt.nonfinite) return fail(QQA_ENONFINITE, "%llu non-finite gradient/state values were produced", stt.nonfinite);
     return QQA_OK;
 }
@@ -886,7 +982,7 @@ extern "C" int qqa_run_step_debug(qqa_run *r, int32_t k, void *stream, float *gr
     if (rc) return rc;
     const int32_t grid = std::min(r->max_grid, r->num_tiles);
     rc = launch_step_chunk(r, 1, grid, st);
-    g_launches += 2;
+    g_launches += 3;
     for (auto &sl : r->slots)
         if (sl.active) sl.t = std::min(sl.t + 1, sl.K);
     r->h_descs[k].grad_dbg = nullptr;

@@ -92,6 +92,33 @@ void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStrea
     advance_kernel<<<(capacity + 127) / 128, 128, 0, st>>>(descs, capacity, nsteps);
 }
 
+// Per-step scalars of the next `nsteps` steps of every active slot, computed
+// once here instead of in every thread of the step kernel:
+//   gamma_t = gamma_min + (gamma_max - gamma_min) t / (K - 1)   (linear schedule, App. C.2)
+//   x = gamma_t * (-2a)   (coefficient of (2p - 1)^(a-1) in the gradient, Eq. 7)
+//   y = lr / (1 - b1^(t+1)),  z = 1 / sqrt(1 - b2^(t+1))   (AdamW bias corrections;
+//   1 - b^k = -expm1(k log1p(b - 1)) avoids cancellation, b - 1 is exact for b in [0.5, 1))
+__global__ void prepare_kernel(const InstDesc *__restrict__ descs, int32_t capacity, int32_t nsteps)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = idx / kMaxChunk, r = idx % kMaxChunk;
+    if (k >= capacity || r >= nsteps) return;
+    const InstDesc &d = descs[k];
+    if (!d.active) return;
+    const int t = d.t + r;
+    if (t >= d.K) return;
+    const float gamma = d.K > 1 ? d.gmin + (d.gmax - d.gmin) * ((float)t / (float)(d.K - 1)) : d.gmin;
+    const float bc1 = -expm1f((float)(t + 1) * log1pf(d.b1 - 1.0f));
+    const float bc2 = -expm1f((float)(t + 1) * log1pf(d.b2 - 1.0f));
+    d.scal[r] = make_float4(gamma * (-2.0f * (float)d.a_ent), d.lr / bc1, rsqrtf(bc2), 0.0f);
+}
+
+void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st)
+{
+    const int total = capacity * kMaxChunk;
+    prepare_kernel<<<(total + 127) / 128, 128, 0, st>>>(descs, capacity, nsteps);
+}
+
 // ---------------------------------------------------------------------------
 // Projection rounding x = [p > 1/2] (Sec. 5) and exact integer costs.
 // A slot is evaluated once per step count (skipped if already evaluated at t).
@@ -131,20 +158,31 @@ __global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, const Tile 
 }
 
 // Per replica: size = sum x_i, inside = #edges (i<j) with x_i x_j, cut = sum w_ij [x_i != x_j].
+// One block per tile: the tile's (row, replica) items are spread over all
+// threads (threads sharing a replica split the rows), partial counts are
+// combined in shared memory, then added to the slot's counters.
 __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
                                   const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile)
 {
+    extern __shared__ long long sh_cnt[];   // [3][S_pad32]
     const int num_tiles = *num_tiles_p;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
         const Tile tl = tiles[tile];
         const InstDesc &d = descs[tl.slot];
         if (!needs_eval(d)) continue;
+        const int S32 = (d.S + 31) & ~31;
+        for (int k = threadIdx.x; k < 3 * S32; k += blockDim.x) sh_cnt[k] = 0;
+        __syncthreads();
         const int row_end = min(tl.row0 + rows_per_tile, d.n);
-        for (int s = threadIdx.x; s < d.S; s += blockDim.x) {
+        const int splits = max(1, (int)blockDim.x / S32);
+        for (int base = threadIdx.x; base < splits * S32; base += blockDim.x) {
+            const int s = base % S32;
+            const int part = base / S32;
+            if (s >= d.S) continue;
             const int w = s >> 5;
             const int b = s & 31;
             long long size = 0, inside = 0, cut = 0;
-            for (int i = tl.row0; i < row_end; ++i) {
+            for (int i = tl.row0 + part; i < row_end; i += splits) {
                 const unsigned xi = (d.bits[(size_t)i * d.W + w] >> b) & 1u;
                 size += xi;
                 const int k1 = d.row_ptr[i + 1];
@@ -156,10 +194,17 @@ __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile
                     if (xi != xj) cut += d.w ? (long long)d.w[k] : 1LL;
                 }
             }
-            if (size) atomicAdd(&d.counts[s], (unsigned long long)size);
-            if (inside) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)inside);
-            if (cut) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)cut);
+            if (size) atomicAdd((unsigned long long *)&sh_cnt[s], (unsigned long long)size);
+            if (inside) atomicAdd((unsigned long long *)&sh_cnt[S32 + s], (unsigned long long)inside);
+            if (cut) atomicAdd((unsigned long long *)&sh_cnt[2 * S32 + s], (unsigned long long)cut);
         }
+        __syncthreads();
+        for (int s = threadIdx.x; s < d.S; s += blockDim.x) {
+            if (sh_cnt[s]) atomicAdd(&d.counts[s], (unsigned long long)sh_cnt[s]);
+            if (sh_cnt[S32 + s]) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)sh_cnt[S32 + s]);
+            if (sh_cnt[2 * S32 + s]) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)sh_cnt[2 * S32 + s]);
+        }
+        __syncthreads();
     }
 }
 
@@ -230,9 +275,9 @@ __global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32
 void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
                  int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st)
 {
-    (void)S_max_pad;
     eval_bits_kernel<<<grid, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile, prec);
-    eval_count_kernel<<<grid, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile);
+    const int S32 = (S_max_pad + 31) & ~31;
+    eval_count_kernel<<<grid, 256, 3 * S32 * sizeof(long long), st>>>(descs, tiles, num_tiles, rows_per_tile);
     eval_finalize_kernel<<<(capacity + 7) / 8, 256, 0, st>>>(descs, capacity);
 }
 

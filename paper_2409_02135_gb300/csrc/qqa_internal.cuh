@@ -39,6 +39,8 @@ struct __align__(16) InstDesc {
     uint32_t *res_bestx;         // [ceil(n/32)]
     long long *hist_best;        // [hist_cap]
     int32_t *hist_step;          // [hist_cap]
+    float4 *scal;                // per-step scalars of the current chunk [kMaxChunk]: x = gamma_t * (-2a),
+                                 // y = lr / (1 - b1^(t+1)), z = 1 / sqrt(1 - b2^(t+1))
     // sizes
     int32_t n, S, S_pad, W;
     int32_t kind, a_ent, t, K;
@@ -46,7 +48,7 @@ struct __align__(16) InstDesc {
     // hyper-parameters
     float lr, wd, b1, b2;
     float adam_eps, gmin, gmax, alpha;
-    float comm_eps, noise_scale, lambda, pad1;
+    float comm_eps, noise_scale, lambda, decay;   // decay = 1 - lr * weight_decay
     uint32_t seed_lo, seed_hi, pad2, pad3;
 };
 
@@ -55,6 +57,10 @@ struct RunStatus {
     unsigned long long nonfinite;   // count of non-finite gradient / state values seen
     unsigned long long timeouts;    // bounded waits that ran out (none in this build's kernels)
 };
+
+// Longest run of steps launched back to back (one chunk); the per-step scalar
+// table of each slot holds this many entries.
+constexpr int kMaxChunk = 64;
 
 // Tiles: (slot, first row). A block processes one tile at a time.
 struct Tile {
@@ -75,10 +81,10 @@ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;   // one widening multiply gives hi and lo
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
@@ -92,21 +98,30 @@ __device__ __forceinline__ float bits_to_unit(uint32_t r)
     return (float)((r >> 8) + 1u) * 5.9604644775390625e-8f;
 }
 
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (x = 0 -> 0).
+__device__ __forceinline__ float sqrt_nonneg(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // Four standard normals for replicas 4q..4q+3 of node i at step t (stream tag 1):
-// Box-Muller on the uniform pairs (r0, r1) and (r2, r3).
+// Box-Muller on the uniform pairs (r0, r1) and (r2, r3): radius sqrt(-2 ln u1),
+// angle 2 pi u2. The angle is taken as 2 pi (u2 - 1/2) - exact in FP32 - so the
+// hardware sine/cosine see (-pi, pi], and the sign flip restores cos/sin(2 pi u2).
 __device__ __forceinline__ void gauss4(uint32_t seed_lo, uint32_t seed_hi, uint32_t i, uint32_t q, uint32_t t,
                                        float out[4])
 {
     const U4 r = philox10(U4{i, q, t, 1u}, seed_lo, seed_hi);
+    const float two_pi = 6.28318530717958647692f;
     float s0, c0, s1, c1;
-    const float rad0 = sqrtf(-2.0f * logf(bits_to_unit(r.x)));
-    sincospif(2.0f * bits_to_unit(r.y), &s0, &c0);
-    const float rad1 = sqrtf(-2.0f * logf(bits_to_unit(r.z)));
-    sincospif(2.0f * bits_to_unit(r.w), &s1, &c1);
-    out[0] = rad0 * c0;
-    out[1] = rad0 * s0;
-    out[2] = rad1 * c1;
-    out[3] = rad1 * s1;
+    const float rad0 = sqrt_nonneg(-2.0f * logf(bits_to_unit(r.x)));
+    __sincosf(two_pi * (bits_to_unit(r.y) - 0.5f), &s0, &c0);
+    const float rad1 = sqrt_nonneg(-2.0f * logf(bits_to_unit(r.z)));
+    __sincosf(two_pi * (bits_to_unit(r.w) - 0.5f), &s1, &c1);
+    out[0] = -rad0 * c0;
+    out[1] = -rad0 * s0;
+    out[2] = -rad1 * c1;
+    out[3] = -rad1 * s1;
 }
 
 // Four uniforms for the initial state (stream tag 0, step 0).
@@ -142,6 +157,21 @@ struct VecT<float> {
     {
         *reinterpret_cast<float4 *>(p) = make_float4(in[0], in[1], in[2], in[3]);
     }
+    __device__ __forceinline__ static void unpack(const uint4 a, float out[4])
+    {
+        out[0] = __uint_as_float(a.x); out[1] = __uint_as_float(a.y);
+        out[2] = __uint_as_float(a.z); out[3] = __uint_as_float(a.w);
+    }
+    // streaming (evict-first) variants for data touched once per step
+    __device__ __forceinline__ static void load_cs(const float *p, float out[4])
+    {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+        out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+    }
+    __device__ __forceinline__ static void store_cs(float *p, const float in[4])
+    {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(in[0], in[1], in[2], in[3]));
+    }
 };
 
 template <>
@@ -164,7 +194,7 @@ struct VecT<__nv_bfloat16> {
     {
         unpack(__ldg(reinterpret_cast<const uint4 *>(p)), out);
     }
-    __device__ __forceinline__ static void store(__nv_bfloat16 *p, const float in[8])
+    __device__ __forceinline__ static uint4 pack(const float in[8])
     {
         uint32_t u[4];
 #pragma unroll
@@ -172,7 +202,19 @@ struct VecT<__nv_bfloat16> {
             const __nv_bfloat162 h = __floats2bfloat162_rn(in[2 * k], in[2 * k + 1]);
             u[k] = *reinterpret_cast<const uint32_t *>(&h);
         }
-        *reinterpret_cast<uint4 *>(p) = make_uint4(u[0], u[1], u[2], u[3]);
+        return make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16 *p, const float in[8])
+    {
+        *reinterpret_cast<uint4 *>(p) = pack(in);
+    }
+    __device__ __forceinline__ static void load_cs(const __nv_bfloat16 *p, float out[8])
+    {
+        unpack(__ldcs(reinterpret_cast<const uint4 *>(p)), out);
+    }
+    __device__ __forceinline__ static void store_cs(__nv_bfloat16 *p, const float in[8])
+    {
+        __stcs(reinterpret_cast<uint4 *>(p), pack(in));
     }
 };
 
@@ -198,6 +240,7 @@ int step_max_active_blocks(int32_t prec, int32_t group_lanes, int32_t vec_per_la
 void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, int32_t prec, cudaStream_t st);
 void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st);
 void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
+void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
                  int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st);
 void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,

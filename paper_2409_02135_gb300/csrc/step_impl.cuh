@@ -1,6 +1,6 @@
-// step_impl.cuh -- the fused PQQA step kernel (one launch per annealing step).
+// step_impl.cuh -- the fused PQQA step kernels (one launch per annealing step).
 //
-// For every (node i, replica s) of every active instance the kernel computes,
+// For every (node i, replica s) of every active instance a step computes,
 // reading only p^t and writing p^{t+1} into the other ping-pong buffer:
 //   Y      = sum_k w_k p^t[col_k][s]            CSR SpMM row, FP32 accumulate in CSR order
 //   g      = MIS:    -1 + lambda Y                                (Eq. 22)
@@ -16,8 +16,19 @@
 // replicas, so a group reads a neighbour row with VPL coalesced 128-bit loads
 // per lane. Neighbour indices are loaded G at a time by the group and
 // broadcast with register shuffles. Row statistics (mean, variance over the S
-// replicas) are group-wide xor-shuffle reductions. Nothing is staged in
-// global memory between the parts: the whole step is one kernel.
+// replicas) are group-wide xor-shuffle reductions.
+//
+// Two kernels share the per-row epilogue and differ in where neighbour rows
+// come from:
+//   qqa_step_kernel       gathers each neighbour row from global memory (L2);
+//                         for sparse graphs, where a row is rarely reused.
+//   qqa_step_tiled_kernel stages consecutive chunks of p^t in shared memory
+//                         with TMA bulk copies (double-buffered, mbarrier
+//                         completion) and serves every neighbour inside the
+//                         chunk from there; for dense graphs, where each staged
+//                         row is reused by many rows of the block.
+// Both accumulate Y in ascending neighbour order, so they give bit-identical
+// results.
 #pragma once
 
 #include "qqa_internal.cuh"
@@ -47,12 +58,310 @@ __device__ __forceinline__ float group_sum(float x, unsigned mask)
     return x;
 }
 
-// 1 - b^k computed without cancellation: -expm1(k * log1p(b - 1)); b - 1 is exact for b in [0.5, 1].
-__device__ __forceinline__ float one_minus_pow(float b, int k)
+// Per-(instance, step) scalars, identical in every thread working on the
+// instance; the t-dependent ones come from the table the prepare kernel fills
+// once per chunk of steps (entry r = step t - t_chunk_start).
+struct StepCtx {
+    int t, n, S, S_pad, kind, half_pow;
+    float ent_coef, decay, step_size, inv_sqrt_bc2, lambda, alpha, noise_scale, b1, b2, adam_eps, comm_eps;
+    const float *cs_cur;
+    float *cs_next;
+    float *grad_dbg;
+};
+
+__device__ __forceinline__ StepCtx make_ctx(const InstDesc *__restrict__ d, int t, int r)
 {
-    return -expm1f((float)k * log1pf(b - 1.0f));
+    StepCtx c;
+    c.t = t;
+    c.n = d->n;
+    c.S = d->S;
+    c.S_pad = d->S_pad;
+    c.kind = d->kind;
+    const float4 sc = d->scal[r];
+    c.ent_coef = sc.x;
+    c.step_size = sc.y;
+    c.inv_sqrt_bc2 = sc.z;
+    c.half_pow = (d->a_ent - 2) / 2;
+    c.decay = d->decay;
+    c.lambda = d->lambda;
+    c.alpha = d->alpha;
+    c.noise_scale = d->noise_scale;
+    c.b1 = d->b1;
+    c.b2 = d->b2;
+    c.adam_eps = d->adam_eps;
+    c.comm_eps = d->comm_eps;
+    c.cs_cur = nullptr;
+    c.cs_next = nullptr;
+    c.grad_dbg = d->grad_dbg;
+    if (c.kind == kMaxClique) {
+        c.cs_cur = d->colsum + (t % 3) * c.S_pad;
+        c.cs_next = d->colsum + ((t + 1) % 3) * c.S_pad;
+    }
+    return c;
 }
 
+// Clique mode: zero the rotating column-sum buffer step t+1 accumulates into
+// (once per instance, by its first tile) and the block's partial sums.
+__device__ __forceinline__ void clique_tile_begin(const InstDesc *__restrict__ d, const StepCtx &c, int row0,
+                                                  float *sh_colsum)
+{
+    if (row0 == 0) {
+        float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
+        for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) cs_zero[s] = 0.0f;
+    }
+    for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) sh_colsum[s] = 0.0f;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void clique_tile_end(const StepCtx &c, const float *sh_colsum)
+{
+    __syncthreads();
+    for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) atomicAdd(c.cs_next + s, sh_colsum[s]);
+    __syncthreads();
+}
+
+// Accumulate Y += w * x for one staged or global neighbour row.
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void accumulate_row(float (&Y)[VPL][VecT<T>::N], const T *rowp, int gl, int S_pad, float w)
+{
+    constexpr int VEC = VecT<T>::N;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int off = (v * G + gl) * VEC;
+        if (off < S_pad) {
+            float x[VEC];
+            VecT<T>::load(rowp + off, x);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
+        }
+    }
+}
+
+// Direct gather of the whole neighbour list of `row` from global memory.
+// Unweighted graphs (MIS, clique, unit max-cut) take a lean path: plain adds
+// (exactly fmaf(1, x, y)) and the weighted degree is the row length.
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, const T *__restrict__ Xc, int row,
+                                              int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
+                                              float &dsum)
+{
+    constexpr int VEC = VecT<T>::N;
+    constexpr int UNR = VPL >= 4 ? 1 : (VPL == 2 ? 2 : 4);   // neighbours in flight per batch
+    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
+    const int32_t *__restrict__ colp = d->col;
+    const int32_t *__restrict__ wp = d->w;
+    // this lane's column offsets; lanes past the padded row read column 0 and discard it
+    int offs[VPL];
+    bool inr[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        offs[v] = (v * G + gl) * VEC;
+        inr[v] = offs[v] < S_pad;
+        if (!inr[v]) offs[v] = 0;
+    }
+    if (wp == nullptr) dsum = (float)(k1 - k0);
+    for (int kb = k0; kb < k1; kb += G) {
+        const int myk = kb + gl;
+        int jl = 0;
+        float wl = 1.0f;
+        if (myk < k1) {
+            jl = __ldg(colp + myk);
+            if (wp) wl = (float)__ldg(wp + myk);
+        }
+        const int cnt = min(G, k1 - kb);
+        int q = 0;
+        for (; q + UNR <= cnt; q += UNR) {
+            uint4 raw[UNR][VPL];   // packed until accumulated: 4 registers per 16-byte slice
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q + u, G) * S_pad;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) raw[u][v] = __ldg(reinterpret_cast<const uint4 *>(rowp + offs[v]));
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const float w = wp ? __shfl_sync(gmask, wl, q + u, G) : 1.0f;
+                if (wp) dsum += w;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    float x[VEC];
+                    VecT<T>::unpack(raw[u][v], x);
+                    if (wp == nullptr) {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) Y[v][e] += x[e];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
+                    }
+                }
+            }
+        }
+        for (; q < cnt; ++q) {
+            const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q, G) * S_pad;
+            const float w = wp ? __shfl_sync(gmask, wl, q, G) : 1.0f;
+            if (wp) dsum += w;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                float x[VEC];
+                VecT<T>::load_ro(rowp + offs[v], x);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+        if (!inr[v]) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Y[v][e] = 0.0f;
+        }
+}
+
+// The row's own data: p (FP32 master or state), the AdamW moments, and the
+// clique column sums. Loaded before the sparse product where registers allow,
+// so their latency overlaps the neighbour gathers.
+template <typename T, int G, int VPL>
+struct OwnRow {
+    float P[VPL][VecT<T>::N];
+    uint4 M[VPL], V[VPL];   // raw 16-byte storage vectors, unpacked when used
+};
+
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void load_own(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
+                                         OwnRow<T, G, VPL> &o)
+{
+    constexpr int VEC = VecT<T>::N;
+    const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[c.t & 1]);
+    const size_t rbase = (size_t)row * c.S_pad;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int off = (v * G + gl) * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) o.P[v][e] = 0.0f;
+        o.M[v] = make_uint4(0, 0, 0, 0);
+        o.V[v] = make_uint4(0, 0, 0, 0);
+        if (off < c.S_pad) {
+            if (d->master) {
+                for (int k = 0; k < VEC; k += 4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(d->master + rbase + off + k);
+                    o.P[v][k] = a.x; o.P[v][k + 1] = a.y; o.P[v][k + 2] = a.z; o.P[v][k + 3] = a.w;
+                }
+            } else {
+                VecT<T>::load(Xc + rbase + off, o.P[v]);
+            }
+            o.M[v] = *reinterpret_cast<const uint4 *>(reinterpret_cast<const T *>(d->m) + rbase + off);
+            o.V[v] = *reinterpret_cast<const uint4 *>(reinterpret_cast<const T *>(d->v) + rbase + off);
+        }
+    }
+}
+
+// Everything after the sparse product for one row: statistics, gradient,
+// AdamW, noise, clamp, stores (and the clique partial column sums).
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
+                                           unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
+                                           const OwnRow<T, G, VPL> &o, RunStatus *__restrict__ status,
+                                           float *colsum_acc)
+{
+    constexpr int VEC = VecT<T>::N;
+    T *__restrict__ Xn = reinterpret_cast<T *>(d->X[(c.t + 1) & 1]);
+    const size_t rbase = (size_t)row * c.S_pad;
+
+    // row statistics over the S replicas (Eq. 10)
+    float mean = 0.0f, inv_std = 0.0f;
+    if (c.alpha != 0.0f) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int nv = c.S - (v * G + gl) * VEC;   // valid replicas in this vector
+            if (nv >= VEC) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) sum += o.P[v][e];
+            } else {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e)
+                    if (e < nv) sum += o.P[v][e];
+            }
+        }
+        mean = group_sum<G>(sum, gmask) / (float)c.S;
+        float sq = 0.0f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int nv = c.S - (v * G + gl) * VEC;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float dl = o.P[v][e] - mean;
+                if (nv >= VEC || e < nv) sq = fmaf(dl, dl, sq);
+            }
+        }
+        inv_std = rsqrtf(group_sum<G>(sq, gmask) / (float)c.S + c.comm_eps);
+    }
+
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int off = (v * G + gl) * VEC;
+        if (off >= c.S_pad) continue;
+        float pn[VEC], M[VEC], V[VEC];
+        VecT<T>::unpack(o.M[v], M);
+        VecT<T>::unpack(o.V[v], V);
+        bool bad = false;
+        // four replicas per Philox call; fully unrolled (register arrays need
+        // compile-time indices)
+#pragma unroll
+        for (int e4 = 0; e4 < VEC; e4 += 4)
+#pragma unroll
+        for (int e = e4; e < e4 + 4; ++e) {
+            float xi[4];
+            if (e == e4) gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)((off + e4) >> 2), (uint32_t)c.t, xi);
+            float csv = 0.0f;
+            if (c.kind == kMaxClique) csv = c.cs_cur[off + e];
+            const float p = o.P[v][e];
+            const float y = Y[v][e];
+            float g;
+            if (c.kind == kMIS) g = fmaf(c.lambda, y, -1.0f);
+            else if (c.kind == kMaxCut) g = fmaf(2.0f, y, -dsum);
+            else g = fmaf(c.lambda, (csv - 0.5f) - y, -1.0f);
+            const float u = fmaf(2.0f, p, -1.0f);
+            const float u2 = u * u;
+            float upow = u * u2;                       // a = 4, the paper's exponent
+            if (c.half_pow != 1) {
+                upow = u;
+                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
+            }
+            g = fmaf(c.ent_coef, upow, g);
+            if (c.alpha != 0.0f) g = fmaf(-c.alpha * inv_std, p - mean, g);
+            if (c.grad_dbg) c.grad_dbg[rbase + off + e] = g;
+            const float mn = fmaf(c.b1, M[e], (1.0f - c.b1) * g);
+            const float vn = fmaf(c.b2, V[e], (1.0f - c.b2) * (g * g));
+            const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
+            float q = p * c.decay;
+            q = fmaf(-c.step_size, __fdividef(mn, denom), q);
+            q = fmaf(c.noise_scale, xi[e - e4], q);
+            bad |= !(fabsf(q) <= 3.0e38f);             // NaN or Inf anywhere upstream lands in q
+            pn[e] = fminf(fmaxf(q, 0.0f), 1.0f);
+            M[e] = mn;
+            V[e] = vn;
+        }
+        if (bad) atomicAdd(&status->nonfinite, 1ULL);
+        VecT<T>::store(Xn + rbase + off, pn);
+        if (d->master) {
+            for (int k = 0; k < VEC; k += 4)
+                *reinterpret_cast<float4 *>(d->master + rbase + off + k) =
+                    make_float4(pn[k], pn[k + 1], pn[k + 2], pn[k + 3]);
+        }
+        VecT<T>::store(reinterpret_cast<T *>(d->m) + rbase + off, M);
+        VecT<T>::store(reinterpret_cast<T *>(d->v) + rbase + off, V);
+        if (c.kind == kMaxClique) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) atomicAdd(colsum_acc + off + e, pn[e]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Direct-gather kernel: a group of G lanes per row, 256 threads per block,
+// (slot, row-block) tiles walked with a grid stride.
+// ---------------------------------------------------------------------------
 template <typename T, int G, int VPL>
 __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restrict__ descs,
                                                        const Tile *__restrict__ tiles,
@@ -61,7 +370,6 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
 {
     constexpr int VEC = VecT<T>::N;
     constexpr int ROWS_PER_WARP = 32 / G;
-    constexpr int UNR = VPL >= 4 ? 1 : (VPL == 2 ? 2 : 4);   // neighbours in flight per batch
     extern __shared__ float sh_colsum[];
 
     const int lane = threadIdx.x & 31;
@@ -76,191 +384,426 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
         const InstDesc *__restrict__ d = descs + tl.slot;
         const int t = d->t + r;
         if (t >= d->K) continue;   // finished instance: whole block skips (same tile)
-
-        const int n = d->n, S = d->S, S_pad = d->S_pad, kind = d->kind;
-        const bool clique = (kind == kMaxClique);
+        const StepCtx c = make_ctx(d, t, r);
+        const bool clique = (c.kind == kMaxClique);
         const int row = tl.row0 + warp * ROWS_PER_WARP + grp;
-
-        // step scalars (identical in every thread of the instance)
-        const float gamma = d->K > 1 ? d->gmin + (d->gmax - d->gmin) * ((float)t / (float)(d->K - 1)) : d->gmin;
-        const float ent_coef = gamma * (-2.0f * (float)d->a_ent);
-        const int half_pow = (d->a_ent - 2) / 2;
-        const float lr = d->lr, b1 = d->b1, b2 = d->b2, adam_eps = d->adam_eps;
-        const float decay = 1.0f - lr * d->wd;
-        const float step_size = lr / one_minus_pow(b1, t + 1);
-        const float inv_sqrt_bc2 = rsqrtf(one_minus_pow(b2, t + 1));
-        const float lambda = d->lambda, alpha = d->alpha, noise_scale = d->noise_scale;
-
-        const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
-        T *__restrict__ Xn = reinterpret_cast<T *>(d->X[(t + 1) & 1]);
-        const float *cs_cur = nullptr;
-        float *cs_next = nullptr;
-        if (clique) {
-            cs_cur = d->colsum + (t % 3) * S_pad;
-            cs_next = d->colsum + ((t + 1) % 3) * S_pad;
-            if (tl.row0 == 0) {   // the rotating buffer used by step t+1 must start at zero
-                float *cs_zero = d->colsum + ((t + 2) % 3) * S_pad;
-                for (int s = threadIdx.x; s < S_pad; s += blockDim.x) cs_zero[s] = 0.0f;
-            }
-            for (int s = threadIdx.x; s < S_pad; s += blockDim.x) sh_colsum[s] = 0.0f;
-            __syncthreads();
-        }
-
-        if (row < n) {
-            const size_t rbase = (size_t)row * S_pad;
-            float P[VPL][VEC];
+        if (clique) clique_tile_begin(d, c, tl.row0, sh_colsum);
+        if (row < c.n) {
+            const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
             float Y[VPL][VEC];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) Y[v][e] = 0.0f;
+            float dsum = 0.0f;
+            OwnRow<T, G, VPL> own;
+            constexpr bool kPrefetch = VPL <= 2;   // own row in flight during the gather
+            if (kPrefetch) load_own<T, G, VPL>(d, c, row, gl, own);
+            gather_direct<T, G, VPL>(d, Xc, row, c.S_pad, gl, gmask, Y, dsum);
+            if (!kPrefetch) load_own<T, G, VPL>(d, c, row, gl, own);
+            update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status, sh_colsum);
+        }
+        if (clique) clique_tile_end(c, sh_colsum);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged kernel. Shared memory: two mbarriers, two chunk buffers of CB
+// rows of p^t each, and the clique partial sums. Each warp owns RPW row
+// groups, so a block covers 8 * RPW * (32 / G) rows; the block streams the
+// chunks that contain its rows' neighbours (from the smallest to the largest
+// neighbour index) and every row consumes, per chunk, the prefix of its
+// remaining (sorted) neighbour list that falls inside the chunk.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bulk (non-tensor) TMA copy global -> shared, completion counted on mbar.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+// Wait for phase `parity` of mbar with a clock limit; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity)
+{
+    const long long start = clock64();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (clock64() - start > (1LL << 31)) return false;   // ~1 s at 2 GHz
+    }
+    return true;
+}
+
+struct TiledSmem {
+    uint64_t mbar[2];
+    int32_t lo, hi;
+    int32_t pad[2];
+};
+
+template <typename T, int G, int VPL, int RPW>
+__global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__restrict__ descs,
+                                                             const Tile *__restrict__ tiles,
+                                                             const int32_t *__restrict__ num_tiles_p,
+                                                             RunStatus *__restrict__ status, int32_t r,
+                                                             int32_t chunk_rows, int32_t buf_elems)
+{
+    constexpr int VEC = VecT<T>::N;
+    constexpr int GPW = 32 / G;   // row groups per warp
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TiledSmem *hdr = reinterpret_cast<TiledSmem *>(smem_raw);
+    T *buf0 = reinterpret_cast<T *>(smem_raw + 128);
+    T *bufs[2] = {buf0, buf0 + buf_elems};
+    float *sh_colsum = reinterpret_cast<float *>(buf0 + 2 * (size_t)buf_elems);
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gl = lane & (G - 1);
+    const int grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int rows_per_block = (blockDim.x >> 5) * RPW * GPW;
+    const int num_tiles = *num_tiles_p;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&hdr->mbar[0], 1);
+        mbar_init(&hdr->mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t uses0 = 0, uses1 = 0;   // completed phases of each buffer's barrier (block-uniform)
+
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        const InstDesc *__restrict__ d = descs + tl.slot;
+        const int t = d->t + r;
+        if (t >= d->K) continue;
+        const StepCtx c = make_ctx(d, t, r);
+        const bool clique = (c.kind == kMaxClique);
+        const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
+        const int32_t *__restrict__ colp = d->col;
+        const int32_t *__restrict__ wp = d->w;
+        const size_t row_bytes = (size_t)c.S_pad * sizeof(T);
+
+        // neighbour range of the block's rows -> chunks to stream
+        if (threadIdx.x == 0) { hdr->lo = 0x7fffffff; hdr->hi = -1; }
+        if (clique) clique_tile_begin(d, c, tl.row0, sh_colsum);
+        else __syncthreads();
+        int kcur[RPW], kend[RPW];
+        float dsum[RPW];
+        float Y[RPW][VPL][VEC];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int row = tl.row0 + (warp * RPW + q) * GPW + grp;
+            kcur[q] = 0;
+            kend[q] = 0;
+            dsum[q] = 0.0f;
+            if (row < c.n) {
+                kcur[q] = __ldg(d->row_ptr + row);
+                kend[q] = __ldg(d->row_ptr + row + 1);
+                if (gl == 0 && kend[q] > kcur[q]) {
+                    atomicMin(&hdr->lo, __ldg(colp + kcur[q]));
+                    atomicMax(&hdr->hi, __ldg(colp + kend[q] - 1));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) Y[q][v][e] = 0.0f;
+        }
+        __syncthreads();
+        const int lo = hdr->lo, hi = hdr->hi;
+        const int c_first = hi >= 0 ? lo / chunk_rows : 0;
+        const int nch = hi >= 0 ? hi / chunk_rows - c_first + 1 : 0;
+
+        auto issue = [&](int ci, int b) {
+            const int node0 = (c_first + ci) * chunk_rows;
+            const int rows = min(chunk_rows, c.n - node0);
+            const uint32_t bytes = (uint32_t)(rows * row_bytes);
+            mbar_arrive_expect_tx(&hdr->mbar[b], bytes);
+            tma_bulk_load(bufs[b], Xc + (size_t)node0 * c.S_pad, bytes, &hdr->mbar[b]);
+        };
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int b = 0; b < 2 && b < nch; ++b) issue(b, b);
+        }
+        bool failed = false;
+        for (int ci = 0; ci < nch; ++ci) {
+            const int b = ci & 1;
+            const uint32_t parity = (b == 0 ? uses0 : uses1) & 1u;
+            const bool ok = mbar_wait_bounded(&hdr->mbar[b], parity);
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            if (b == 0) ++uses0; else ++uses1;
+            const int node0 = (c_first + ci) * chunk_rows;
+            const int node_end = node0 + chunk_rows;
+            const T *sb = bufs[b];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                int k = kcur[q];
+                const int ke = kend[q];
+                while (k < ke) {   // group-uniform loop
+                    const int myk = k + gl;
+                    int jl = 0x7fffffff;
+                    float wl = 1.0f;
+                    if (myk < ke) {
+                        jl = __ldg(colp + myk);
+                        if (wp) wl = (float)__ldg(wp + myk);
+                    }
+                    const unsigned in = __ballot_sync(gmask, jl < node_end);
+                    const int cnt = __popc(G == 32 ? in : ((in >> (grp * G)) & ((1u << G) - 1u)));
+                    for (int u = 0; u < cnt; ++u) {
+                        const int j = __shfl_sync(gmask, jl, u, G);
+                        const float w = wp ? __shfl_sync(gmask, wl, u, G) : 1.0f;
+                        dsum[q] += w;
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j - node0) * c.S_pad, gl, c.S_pad, w);
+                    }
+                    k += cnt;
+                    if (cnt < G) break;
+                }
+                kcur[q] = k;
+            }
+            __syncthreads();   // every thread is done with buffer b
+            if (threadIdx.x == 0 && ci + 2 < nch) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(ci + 2, b);
+            }
+        }
+        if (failed) {
+            // a staged copy did not arrive in time: flag it, let any copy still
+            // in flight land (bounded), and leave without touching the state
+            if (threadIdx.x == 0) {
+                atomicAdd(&status->timeouts, 1ULL);
+                mbar_wait_bounded(&hdr->mbar[0], uses0 & 1u);
+                mbar_wait_bounded(&hdr->mbar[1], uses1 & 1u);
+            }
+            __syncthreads();
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int row = tl.row0 + (warp * RPW + q) * GPW + grp;
+            if (row < c.n) {
+                OwnRow<T, G, VPL> own;
+                load_own<T, G, VPL>(d, c, row, gl, own);
+                update_row<T, G, VPL>(d, c, row, gl, gmask, Y[q], dsum[q], own, status, sh_colsum);
+            }
+        }
+        if (clique) clique_tile_end(c, sh_colsum);
+        else __syncthreads();   // hdr->lo / hi are rewritten by the next tile
+        (void)rows_per_block;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Streaming kernel for sparse graphs: each thread keeps a private, double-
+// buffered prefetch area in shared memory. While it computes row i it has
+// already asked, with cp.async (16 bytes per request, L2-only caching), for
+// exactly the 16-byte slices of row i+1 it will need: its own p (FP32 master or
+// state), m and v, and the slices of the first NB neighbour rows. Completion is
+// tracked per thread by cp.async.wait_group, so no barrier or spin-wait is
+// involved; neighbours beyond NB are gathered directly, after the prefetched
+// ones, which keeps the ascending accumulation order of the other kernels.
+// Max-clique partial column sums go straight to global memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+struct StreamItem {
+    const InstDesc *d;
+    int row, t, k0, k1;
+    bool exists, valid;
+};
+
+template <typename T, int G, int VPL, int NB>
+__global__ void __launch_bounds__(256) qqa_step_stream_kernel(const InstDesc *__restrict__ descs,
+                                                              const Tile *__restrict__ tiles,
+                                                              const int32_t *__restrict__ num_tiles_p,
+                                                              RunStatus *__restrict__ status, int32_t r)
+{
+    constexpr int VEC = VecT<T>::N;
+    constexpr int GPW = 32 / G;
+    constexpr int PW = sizeof(T) == 2 ? 2 : 1;   // 16-byte words of the own p slice (FP32 master for BF16)
+    constexpr int SLOTS = PW + 2 + NB;          // p, m, v, neighbours
+    extern __shared__ uint4 sh_pf[];            // [2][VPL][SLOTS][blockDim]
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gl = lane & (G - 1);
+    const int grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int num_tiles = *num_tiles_p;
+    const int nthr = blockDim.x;
+    auto slot_ptr = [&](int stage, int v, int slot) -> uint4 * {
+        return sh_pf + ((size_t)((stage * VPL + v) * SLOTS + slot)) * nthr + threadIdx.x;
+    };
+
+    auto fetch = [&](int it) -> StreamItem {
+        StreamItem x;
+        const int tile = blockIdx.x + it * gridDim.x;
+        x.exists = tile < num_tiles;
+        x.valid = false;
+        x.d = nullptr;
+        x.row = x.t = x.k0 = x.k1 = 0;
+        if (!x.exists) return x;
+        const Tile tl = tiles[tile];
+        x.d = descs + tl.slot;
+        x.t = x.d->t + r;
+        x.row = tl.row0 + warp * GPW + grp;
+        x.valid = x.t < x.d->K && x.row < x.d->n;
+        if (x.valid) {
+            x.k0 = __ldg(x.d->row_ptr + x.row);
+            x.k1 = __ldg(x.d->row_ptr + x.row + 1);
+        }
+        return x;
+    };
+
+    // ask for the slices of item x this thread will read, into `stage`
+    auto request = [&](const StreamItem &x, int stage) {
+        const InstDesc *__restrict__ d = x.d;
+        const int S_pad = d->S_pad;
+        const size_t rbase = (size_t)x.row * S_pad;
+        const T *Xc = reinterpret_cast<const T *>(d->X[x.t & 1]);
+        const int npf = min(x.k1 - x.k0, NB);
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int off = (v * G + gl) * VEC;
+            if (off < S_pad) {
+                if (d->master) {
+                    cp_async16(slot_ptr(stage, v, 0), d->master + rbase + off);
+                    if (PW == 2) cp_async16(slot_ptr(stage, v, PW - 1), d->master + rbase + off + 4);
+                } else {
+                    cp_async16(slot_ptr(stage, v, 0), Xc + rbase + off);
+                }
+                cp_async16(slot_ptr(stage, v, PW), reinterpret_cast<const T *>(d->m) + rbase + off);
+                cp_async16(slot_ptr(stage, v, PW + 1), reinterpret_cast<const T *>(d->v) + rbase + off);
+            }
+        }
+        // neighbour indices are read G at a time by the group and broadcast
+        for (int qb = 0; qb < npf; qb += G) {
+            const int jl = qb + gl < npf ? __ldg(d->col + x.k0 + qb + gl) : 0;
+            const int qn = min(G, npf - qb);
+            for (int q = 0; q < qn; ++q) {
+                const int j = __shfl_sync(gmask, jl, q, G);
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    const int off = (v * G + gl) * VEC;
+                    if (off < S_pad) cp_async16(slot_ptr(stage, v, PW + 2 + qb + q), Xc + (size_t)j * S_pad + off);
+                }
+            }
+        }
+    };
+
+    StreamItem cur = fetch(0);
+    if (cur.valid) request(cur, 0);
+    cp_async_commit();
+    for (int it = 0; cur.exists; ++it) {
+        const int stage = it & 1;
+        StreamItem nxt = fetch(it + 1);
+        if (nxt.valid) request(nxt, stage ^ 1);
+        cp_async_commit();
+        cp_async_wait_1();   // everything but the newest group has landed: cur's slices
+        if (cur.valid) {
+            const InstDesc *__restrict__ d = cur.d;
+            const StepCtx c = make_ctx(d, cur.t, r);
+            if (c.kind == kMaxClique && cur.row == 0) {
+                float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
+                for (int s2 = gl; s2 < c.S_pad; s2 += G) cs_zero[s2] = 0.0f;
+            }
+            OwnRow<T, G, VPL> own;
+            float Y[VPL][VEC];
+            float dsum = 0.0f;
+            const int deg = cur.k1 - cur.k0;
+            const int npf = min(deg, NB);
+            const int32_t *__restrict__ wp = d->w;
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 const int off = (v * G + gl) * VEC;
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) { Y[v][e] = 0.0f; P[v][e] = 0.0f; }
-                if (off < S_pad) {
-                    if (d->master) load_f32_vec(d->master + rbase + off, P[v], VEC);
-                    else VecT<T>::load(Xc + rbase + off, P[v]);
+                for (int e = 0; e < VEC; ++e) { Y[v][e] = 0.0f; own.P[v][e] = 0.0f; }
+                own.M[v] = make_uint4(0, 0, 0, 0);
+                own.V[v] = make_uint4(0, 0, 0, 0);
+                if (off < c.S_pad) {
+                    if (d->master) {
+                        const uint4 a = *slot_ptr(stage, v, 0);
+                        own.P[v][0] = __uint_as_float(a.x); own.P[v][1] = __uint_as_float(a.y);
+                        own.P[v][2] = __uint_as_float(a.z); own.P[v][3] = __uint_as_float(a.w);
+                        if (PW == 2) {
+                            const uint4 b = *slot_ptr(stage, v, PW - 1);
+                            own.P[v][4] = __uint_as_float(b.x); own.P[v][5] = __uint_as_float(b.y);
+                            own.P[v][6] = __uint_as_float(b.z); own.P[v][7] = __uint_as_float(b.w);
+                        }
+                    } else {
+                        VecT<T>::unpack(*slot_ptr(stage, v, 0), own.P[v]);
+                    }
+                    own.M[v] = *slot_ptr(stage, v, PW);
+                    own.V[v] = *slot_ptr(stage, v, PW + 1);
                 }
             }
-
-            // ---- CSR SpMM row: Y = sum_k w_k X^t[col_k] -----------------
-            const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
-            const int32_t *__restrict__ colp = d->col;
-            const int32_t *__restrict__ wp = d->w;
-            float dsum = 0.0f;
-            for (int kb = k0; kb < k1; kb += G) {
-                const int myk = kb + gl;
-                int jl = 0;
-                float wl = 1.0f;
-                if (myk < k1) {
-                    jl = __ldg(colp + myk);
-                    if (wp) wl = (float)__ldg(wp + myk);
-                }
-                const int cnt = min(G, k1 - kb);
-                int q = 0;
-                for (; q + UNR <= cnt; q += UNR) {
-                    int j[UNR];
-                    float wq[UNR];
-                    float xv[UNR][VPL][VEC];
+            // prefetched neighbours, then the rest straight from global memory
+            for (int q = 0; q < npf; ++q) {
+                const float w = wp ? (float)__ldg(wp + cur.k0 + q) : 1.0f;
+                dsum += w;
 #pragma unroll
-                    for (int u = 0; u < UNR; ++u) {
-                        j[u] = __shfl_sync(gmask, jl, q + u, G);
-                        wq[u] = wp ? __shfl_sync(gmask, wl, q + u, G) : 1.0f;
-                    }
+                for (int v = 0; v < VPL; ++v) {
+                    const int off = (v * G + gl) * VEC;
+                    if (off < c.S_pad) {
+                        float x[VEC];
+                        VecT<T>::unpack(*slot_ptr(stage, v, PW + 2 + q), x);
 #pragma unroll
-                    for (int u = 0; u < UNR; ++u)
-#pragma unroll
-                        for (int v = 0; v < VPL; ++v) {
-                            const int off = (v * G + gl) * VEC;
-                            if (off < S_pad) VecT<T>::load_ro(Xc + (size_t)j[u] * S_pad + off, xv[u][v]);
-                            else {
-#pragma unroll
-                                for (int e = 0; e < VEC; ++e) xv[u][v][e] = 0.0f;
-                            }
-                        }
-#pragma unroll
-                    for (int u = 0; u < UNR; ++u) {
-                        dsum += wq[u];
-#pragma unroll
-                        for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                            for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(wq[u], xv[u][v][e], Y[v][e]);
+                        for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
                     }
                 }
-                for (; q < cnt; ++q) {
-                    const int jj = __shfl_sync(gmask, jl, q, G);
-                    const float ww = wp ? __shfl_sync(gmask, wl, q, G) : 1.0f;
-                    dsum += ww;
+            }
+            if (deg > NB) {
+                const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[c.t & 1]);
+                for (int k = cur.k0 + NB; k < cur.k1; ++k) {
+                    const int j = __ldg(d->col + k);
+                    const float w = wp ? (float)__ldg(wp + k) : 1.0f;
+                    dsum += w;
 #pragma unroll
                     for (int v = 0; v < VPL; ++v) {
                         const int off = (v * G + gl) * VEC;
-                        if (off < S_pad) {
+                        if (off < c.S_pad) {
                             float x[VEC];
-                            VecT<T>::load_ro(Xc + (size_t)jj * S_pad + off, x);
+                            VecT<T>::load_ro(Xc + (size_t)j * c.S_pad + off, x);
 #pragma unroll
-                            for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(ww, x[e], Y[v][e]);
+                            for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
                         }
                     }
                 }
             }
-
-            // ---- row statistics over the S replicas (Eq. 10) ----------
-            float mean = 0.0f, inv_std = 0.0f;
-            if (alpha != 0.0f) {
-                float sum = 0.0f;
-#pragma unroll
-                for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if ((v * G + gl) * VEC + e < S) sum += P[v][e];
-                mean = group_sum<G>(sum, gmask) / (float)S;
-                float sq = 0.0f;
-#pragma unroll
-                for (int v = 0; v < VPL; ++v)
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e)
-                        if ((v * G + gl) * VEC + e < S) {
-                            const float dl = P[v][e] - mean;
-                            sq = fmaf(dl, dl, sq);
-                        }
-                inv_std = rsqrtf(group_sum<G>(sq, gmask) / (float)S + d->comm_eps);
-            }
-
-            // ---- gradient, AdamW, noise, clamp, store -----------------
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const int off = (v * G + gl) * VEC;
-                if (off >= S_pad) continue;
-                float M[VEC], V[VEC], xi[VEC], pn[VEC];
-                VecT<T>::load(reinterpret_cast<const T *>(d->m) + rbase + off, M);
-                VecT<T>::load(reinterpret_cast<const T *>(d->v) + rbase + off, V);
-#pragma unroll
-                for (int k = 0; k < VEC / 4; ++k)
-                    gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)((off >> 2) + k), (uint32_t)t, xi + 4 * k);
-                float csv[VEC];
-                if (clique) load_f32_vec(cs_cur + off, csv, VEC);
-                bool bad = false;
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) {
-                    const float p = P[v][e];
-                    const float y = Y[v][e];
-                    float g;
-                    if (kind == kMIS) g = fmaf(lambda, y, -1.0f);
-                    else if (kind == kMaxCut) g = fmaf(2.0f, y, -dsum);
-                    else g = fmaf(lambda, (csv[e] - 0.5f) - y, -1.0f);
-                    const float u = fmaf(2.0f, p, -1.0f);
-                    float upow = u;
-                    const float u2 = u * u;
-                    for (int k = 0; k < half_pow; ++k) upow *= u2;
-                    g = fmaf(ent_coef, upow, g);
-                    if (alpha != 0.0f) g = fmaf(-alpha * inv_std, p - mean, g);
-                    if (d->grad_dbg) d->grad_dbg[rbase + off + e] = g;
-                    const float mn = fmaf(b1, M[e], (1.0f - b1) * g);
-                    const float vn = fmaf(b2, V[e], (1.0f - b2) * (g * g));
-                    const float denom = fmaf(sqrtf(vn), inv_sqrt_bc2, adam_eps);
-                    float q = p * decay;
-                    q = fmaf(-step_size, mn / denom, q);
-                    q = fmaf(noise_scale, xi[e], q);
-                    bad |= !(fabsf(q) <= 3.0e38f) || !(fabsf(g) <= 3.0e38f);
-                    pn[e] = fminf(fmaxf(q, 0.0f), 1.0f);
-                    M[e] = mn;
-                    V[e] = vn;
-                }
-                if (bad) atomicAdd(&status->nonfinite, 1ULL);
-                VecT<T>::store(Xn + rbase + off, pn);
-                if (d->master) store_f32_vec(d->master + rbase + off, pn, VEC);
-                VecT<T>::store(reinterpret_cast<T *>(d->m) + rbase + off, M);
-                VecT<T>::store(reinterpret_cast<T *>(d->v) + rbase + off, V);
-                if (clique) {
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) atomicAdd(sh_colsum + off + e, pn[e]);
-                }
-            }
+            update_row<T, G, VPL>(d, c, cur.row, gl, gmask, Y, dsum, own, status, c.cs_next);
         }
-
-        if (clique) {
-            __syncthreads();
-            for (int s = threadIdx.x; s < S_pad; s += blockDim.x) atomicAdd(cs_next + s, sh_colsum[s]);
-            __syncthreads();
-        }
+        cur = nxt;
     }
 }
 

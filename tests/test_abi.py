@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header(lib):
     from paper_2409_02135_gb300._lib import qqa_params, qqa_launch_config
     assert ctypes.sizeof(qqa_params) == 80
-    assert ctypes.sizeof(qqa_launch_config) == 24
+    assert ctypes.sizeof(qqa_launch_config) == 32
     p = qqa_params()
     lib.qqa_default_params(ctypes.byref(p))
     assert (p.S, p.a_ent, p.lam, p.gamma_min, p.gamma_max) == (128, 4, 2.0, -2.0, pytest.approx(0.1))

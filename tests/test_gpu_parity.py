@@ -101,7 +101,7 @@ def test_single_step_every_layout(cfg):
     G_, V_, B_ = cfg
     g = _graph(MIS, 130, 0.1, 6)
     p = Params(S=16, steps=50, alpha_comm=0.5, seed=2)
-    run = make_run(MIS, g, p, config=qqa.LaunchConfig(G_, V_, B_))
+    run = make_run(MIS, g, p, config=qqa.LaunchConfig(G_, V_, B_, kernel=qqa.KERNEL_DIRECT))
     c = run.config()
     assert (c.group_lanes, c.vec_per_lane, c.block_threads) == cfg
     run.steps(3)
@@ -128,6 +128,78 @@ def test_isolated_nodes_single_node_and_ragged_tiles():
     g1 = G.from_edges(1, [], [])
     run1 = make_run(MAXCUT, g1, p)
     _check_step(MAXCUT, g1, p, FP32, run1)
+
+
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("prec,S,layout", [(FP32, 128, (32, 1, 4)), (FP32, 128, (32, 1, 8)), (FP32, 200, (32, 2, 2)),
+                                           (FP32, 30, (8, 1, 4)), (BF16, 256, (32, 1, 2)), (BF16, 100, (16, 1, 8)),
+                                           (FP32, 64, (16, 1, 2)), (BF16, 24, (4, 1, 4))])
+def test_staged_kernel_equals_direct_kernel(kind, prec, S, layout):
+    """The TMA-staged kernel reads neighbour rows from shared memory in the same
+    ascending order as the direct gather, so states are bit-identical."""
+    G_, V_, R_ = layout
+    g = _graph(kind, 357, 0.12, 50 + kind, weighted=(kind == MAXCUT))
+    p = Params(S=S, steps=100, alpha_comm=0.3, seed=11, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    a = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, 256, kernel=qqa.KERNEL_STAGED, kernel_param=R_))
+    b = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, 256, kernel=qqa.KERNEL_DIRECT))
+    assert a.config().kernel == qqa.KERNEL_STAGED and b.config().kernel == qqa.KERNEL_DIRECT
+    a.steps(60)
+    b.steps(60)
+    Xa, ma, va, _ = a.get_state(0)
+    Xb, mb, vb, _ = b.get_state(0)
+    if kind == MAXCLIQUE:   # column sums are float atomics: order-dependent rounding
+        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
+    else:
+        np.testing.assert_array_equal(Xa, Xb)
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+
+
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("prec,S,layout", [(BF16, 256, (32, 1, 8)), (BF16, 256, (32, 1, 4)), (FP32, 128, (32, 1, 8)),
+                                           (FP32, 200, (32, 2, 4)), (FP32, 30, (8, 1, 8)), (BF16, 40, (8, 1, 4)),
+                                           (FP32, 8, (2, 1, 8))])
+def test_stream_kernel_equals_direct_kernel(kind, prec, S, layout):
+    """The cp.async streaming kernel (prefetched and overflow neighbours in CSR
+    order) gives the direct kernel's states bit for bit; graphs mix rows with
+    fewer and more neighbours than the prefetch depth."""
+    G_, V_, NB = layout
+    g = G.barabasi_albert(413, 3, 70 + kind)
+    if kind == MAXCUT:
+        rng = np.random.default_rng(kind)
+        u, v, _ = g.upper_edges()
+        g = G.from_edges(g.n, u, v, rng.integers(-2, 5, size=u.size))
+    p = Params(S=S, steps=100, alpha_comm=0.3, seed=12, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    a = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, 256, kernel=qqa.KERNEL_STREAM, kernel_param=NB))
+    b = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, 256, kernel=qqa.KERNEL_DIRECT))
+    assert a.config().kernel == qqa.KERNEL_STREAM
+    a.steps(60)
+    b.steps(60)
+    Xa, ma, va, _ = a.get_state(0)
+    Xb, mb, vb, _ = b.get_state(0)
+    if kind == MAXCLIQUE:
+        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
+    else:
+        np.testing.assert_array_equal(Xa, Xb)
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+
+
+def test_stream_kernel_single_step_parity_sparse_graph():
+    g = G.random_regular(2000, 3, 4)
+    p = Params(S=256, steps=500, alpha_comm=0.3, seed=0, precision=BF16, gamma_min=-5.0)
+    run = make_run(MAXCUT, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_STREAM))
+    run.steps(20)
+    _check_step(MAXCUT, g, p, BF16, run)
+
+
+def test_staged_kernel_single_step_parity_dense_graph():
+    g = G.erdos_renyi(750, 0.15, 1000)
+    p = Params(S=128, steps=3000, alpha_comm=0.3, seed=0)
+    run = make_run(MIS, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_STAGED))
+    assert run.config().kernel == qqa.KERNEL_STAGED
+    run.steps(50)
+    _check_step(MIS, g, p, FP32, run)
 
 
 # ---------------------------------------------------------- multi-step ---

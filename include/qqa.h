@@ -250,6 +250,39 @@ int qqa_run_set_state(qqa_run *r, int32_t slot, void *stream, const float *X, co
  */
 int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
 
+/* ------------------------------------------------------ no allocation */
+/*
+ * Projection rounding and exact costs (the same results as qqa_round_eval) of
+ * a replica state held in caller-owned device memory, using no device
+ * allocation at all. The paper has no counterpart: this is for callers that
+ * must not allocate device memory when they evaluate - a serving loop that
+ * budgets HBM up front and cannot let a request fail on, or stall behind, an
+ * allocation, or a framework that owns all device memory itself.
+ *   kind, n          : problem kind and node count
+ *   nnz              : row_ptr[n]
+ *   row_ptr, col, w  : DEVICE CSR arrays as for qqa_create_problem (w NULL =
+ *                      unit weights; max-cut only). Not validated on the host;
+ *                      the kernels skip out-of-range indices instead of
+ *                      reading out of bounds.
+ *   S, ld, X         : DEVICE float X[n][ld], replica s of node i at i*ld + s,
+ *                      1 <= S <= 1024, S <= ld
+ *   lambda           : penalty coefficient of the energy
+ *   obj, viol        : DEVICE int64[S]; feasible: DEVICE uint8[S];
+ *   energy           : DEVICE double[S]; best_s: DEVICE int32[1]
+ *                      (conventions as qqa_run_result)
+ *   stream           : cudaStream_t; the call is asynchronous
+ * Scratch: a static device array of a little over 4 MiB that every GPU which
+ * loads the library holds until exit; n * ceil(S/32) must not exceed 1048576,
+ * else QQA_EINVAL. Every call shares that array, so calls whose work overlaps
+ * on the GPU race. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins. Error messages: qqa_noalloc_last_error().
+ */
+int qqa_round_eval_noalloc(int32_t kind, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
+                           const int32_t *w, int32_t S, int64_t ld, const float *X, float lambda, int64_t *obj,
+                           int64_t *viol, uint8_t *feasible, double *energy, int32_t *best_s, void *stream);
+const char *qqa_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -270,6 +270,23 @@ class Run:
         return g
 
 
+def round_eval_noalloc(kind: int, n: int, nnz: int, row_ptr, col, w, S: int, ld: int, X, lam: float,
+                       obj, viol, feasible, energy, best_s, stream=None):
+    """qqa_round_eval_noalloc: evaluate a state held in caller-owned device
+    memory without any device allocation (for callers that must not allocate
+    while they evaluate). All array arguments are device addresses (ints) or
+    objects with data_ptr(); w may be None."""
+    def addr(a):
+        if a is None:
+            return None
+        return int(a.data_ptr()) if hasattr(a, "data_ptr") else int(a)
+    rc = load().qqa_round_eval_noalloc(int(kind), int(n), int(nnz), addr(row_ptr), addr(col), addr(w), int(S),
+                                       int(ld), addr(X), float(lam), addr(obj), addr(viol), addr(feasible),
+                                       addr(energy), addr(best_s), stream_handle(stream))
+    if rc != QQA_OK:
+        raise QQAError(rc, load().qqa_noalloc_last_error().decode(errors="replace"))
+
+
 def anneal(problems, params, config=None, stream=None, allocator=None) -> Run:
     """Whole anneal (qqa_anneal): init, K steps with periodic rounding, final evaluation."""
     ps = (qqa_params * len(problems))(*params)

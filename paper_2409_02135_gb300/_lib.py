@@ -94,6 +94,9 @@ SIGNATURES = {
     "qqa_run_get_state": (ctypes.c_int, [_P, _I32, _P, _PF, _PF, _PF, _PI32]),
     "qqa_run_set_state": (ctypes.c_int, [_P, _I32, _P, _PF, _PF, _PF, _I32]),
     "qqa_run_step_debug": (ctypes.c_int, [_P, _I32, _P, _PF]),
+    "qqa_round_eval_noalloc": (ctypes.c_int, [_I32, _I32, ctypes.c_int64, _P, _P, _P, _I32, ctypes.c_int64, _P,
+                                              ctypes.c_float, _P, _P, _P, _P, _P, _P]),
+    "qqa_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None

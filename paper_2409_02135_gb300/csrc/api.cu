@@ -257,6 +257,7 @@ struct qqa_run {
 };
 
 static const bool kAutoStaged = false;
+static const int kTiledIdxCapHost = 8192;   // must equal kTiledIdxCap in step_impl.cuh
 
 static int pick_layout(int32_t S_pad, int32_t vec, int32_t &G, int32_t &VPL)
 {
@@ -312,7 +313,8 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         const int row_bytes = r->S_max_pad * tb;
         r->chunk_rows = std::max(8, 32768 / row_bytes);
         r->buf_elems = r->chunk_rows * r->S_max_pad;
-        r->smem = 128 + 2 * r->buf_elems * tb + r->S_max_pad * (int)sizeof(float);
+        // header, two chunk buffers, clique partial sums (1024 floats), CSR index segment
+        r->smem = 128 + 2 * r->buf_elems * tb + 1024 * (int)sizeof(float) + kTiledIdxCapHost * (int)sizeof(int32_t);
         QQA_CK(cudaFuncSetAttribute(r->tiled_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
         QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->tiled_fn, block, r->smem));
         r->rows_per_tile = (block / 32) * rpw * (32 / G);

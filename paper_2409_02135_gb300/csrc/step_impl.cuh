@@ -467,6 +467,9 @@ struct TiledSmem {
     int32_t pad[2];
 };
 
+// Capacity (ints) of the shared-memory copy of a tile's CSR index segment.
+constexpr int kTiledIdxCap = 8192;
+
 template <typename T, int G, int VPL, int RPW>
 __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__restrict__ descs,
                                                              const Tile *__restrict__ tiles,
@@ -481,6 +484,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
     T *buf0 = reinterpret_cast<T *>(smem_raw + 128);
     T *bufs[2] = {buf0, buf0 + buf_elems};
     float *sh_colsum = reinterpret_cast<float *>(buf0 + 2 * (size_t)buf_elems);
+    int32_t *sidx = reinterpret_cast<int32_t *>(sh_colsum + 1024);   // colsum region holds up to 1024 floats
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -526,6 +530,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
             if (row < c.n) {
                 kcur[q] = __ldg(d->row_ptr + row);
                 kend[q] = __ldg(d->row_ptr + row + 1);
+                if (wp == nullptr) dsum[q] = (float)(kend[q] - kcur[q]);
                 if (gl == 0 && kend[q] > kcur[q]) {
                     atomicMin(&hdr->lo, __ldg(colp + kcur[q]));
                     atomicMax(&hdr->hi, __ldg(colp + kend[q] - 1));
@@ -536,6 +541,12 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) Y[q][v][e] = 0.0f;
         }
+        // the tile's CSR index segment, copied to shared memory when it fits
+        const int seg0 = __ldg(d->row_ptr + tl.row0);
+        const int seg1 = __ldg(d->row_ptr + min(tl.row0 + rows_per_block, c.n));
+        const bool staged_idx = wp == nullptr && seg1 - seg0 <= kTiledIdxCap;
+        if (staged_idx)
+            for (int k = threadIdx.x; k < seg1 - seg0; k += blockDim.x) sidx[k] = __ldg(colp + seg0 + k);
         __syncthreads();
         const int lo = hdr->lo, hi = hdr->hi;
         const int c_first = hi >= 0 ? lo / chunk_rows : 0;
@@ -562,30 +573,57 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
             const int node0 = (c_first + ci) * chunk_rows;
             const int node_end = node0 + chunk_rows;
             const T *sb = bufs[b];
+            if (staged_idx) {
+                // indices from shared memory (broadcast reads), four at a time while
+                // the fourth is still inside the chunk (rows are sorted)
 #pragma unroll
-            for (int q = 0; q < RPW; ++q) {
-                int k = kcur[q];
-                const int ke = kend[q];
-                while (k < ke) {   // group-uniform loop
-                    const int myk = k + gl;
-                    int jl = 0x7fffffff;
-                    float wl = 1.0f;
-                    if (myk < ke) {
-                        jl = __ldg(colp + myk);
-                        if (wp) wl = (float)__ldg(wp + myk);
+                for (int q = 0; q < RPW; ++q) {
+                    int k = kcur[q];
+                    const int ke = kend[q];
+                    while (k + 4 <= ke) {
+                        const int j0 = sidx[k - seg0], j1 = sidx[k + 1 - seg0];
+                        const int j2 = sidx[k + 2 - seg0], j3 = sidx[k + 3 - seg0];
+                        if (j3 >= node_end) break;
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j0 - node0) * c.S_pad, gl, c.S_pad, 1.0f);
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j1 - node0) * c.S_pad, gl, c.S_pad, 1.0f);
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j2 - node0) * c.S_pad, gl, c.S_pad, 1.0f);
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j3 - node0) * c.S_pad, gl, c.S_pad, 1.0f);
+                        k += 4;
                     }
-                    const unsigned in = __ballot_sync(gmask, jl < node_end);
-                    const int cnt = __popc(G == 32 ? in : ((in >> (grp * G)) & ((1u << G) - 1u)));
-                    for (int u = 0; u < cnt; ++u) {
-                        const int j = __shfl_sync(gmask, jl, u, G);
-                        const float w = wp ? __shfl_sync(gmask, wl, u, G) : 1.0f;
-                        dsum[q] += w;
-                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j - node0) * c.S_pad, gl, c.S_pad, w);
+                    while (k < ke) {
+                        const int j = sidx[k - seg0];
+                        if (j >= node_end) break;
+                        accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j - node0) * c.S_pad, gl, c.S_pad, 1.0f);
+                        ++k;
                     }
-                    k += cnt;
-                    if (cnt < G) break;
+                    kcur[q] = k;
                 }
-                kcur[q] = k;
+            } else {
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    int k = kcur[q];
+                    const int ke = kend[q];
+                    while (k < ke) {   // group-uniform loop
+                        const int myk = k + gl;
+                        int jl = 0x7fffffff;
+                        float wl = 1.0f;
+                        if (myk < ke) {
+                            jl = __ldg(colp + myk);
+                            if (wp) wl = (float)__ldg(wp + myk);
+                        }
+                        const unsigned in = __ballot_sync(gmask, jl < node_end);
+                        const int cnt = __popc(G == 32 ? in : ((in >> (grp * G)) & ((1u << G) - 1u)));
+                        for (int u = 0; u < cnt; ++u) {
+                            const int j = __shfl_sync(gmask, jl, u, G);
+                            const float w = wp ? __shfl_sync(gmask, wl, u, G) : 1.0f;
+                            if (wp) dsum[q] += w;
+                            accumulate_row<T, G, VPL>(Y[q], sb + (size_t)(j - node0) * c.S_pad, gl, c.S_pad, w);
+                        }
+                        k += cnt;
+                        if (cnt < G) break;
+                    }
+                    kcur[q] = k;
+                }
             }
             __syncthreads();   // every thread is done with buffer b
             if (threadIdx.x == 0 && ci + 2 < nch) {
@@ -614,8 +652,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
             }
         }
         if (clique) clique_tile_end(c, sh_colsum);
-        else __syncthreads();   // hdr->lo / hi are rewritten by the next tile
-        (void)rows_per_block;
+        else __syncthreads();   // hdr->lo / hi and sidx are rewritten by the next tile
     }
 }
 

@@ -258,6 +258,10 @@ def run_ours(args):
     cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3}[args.kernel],
                            kernel_param=args.kernel_param, group_lanes=args.group_lanes,
                            vec_per_lane=args.vec_per_lane, block_threads=args.block_threads)
+    tuned_us = None
+    if args.autotune and args.kernel == "auto" and not (args.group_lanes or args.vec_per_lane or args.block_threads):
+        cfg, tuned_us = qqa.autotune(probs, params, trial_steps=100, stream=stream, allocator=alloc)
+        cfg.use_graphs = 1
     run = qqa.Run.create(probs, params, config=cfg, stream=stream, allocator=alloc)
     K = max(p.steps for p in params)
     R = min(p.round_every for p in params) or K
@@ -366,7 +370,7 @@ def run_ours(args):
                               "group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
                               "kernel_param": run.config().kernel_param,
                               "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
-                              "graphs": True}},
+                              "graphs": True, "autotuned": tuned_us is not None}},
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
         "gpu_launches": launches, "clocks": clocks.summary(),
         "replica_node_updates_per_s": sum_over_ranks(sum(i.graph.n * i.params.S * i.params.steps
@@ -394,6 +398,8 @@ def main():
     ap.add_argument("--group-lanes", type=int, default=0)
     ap.add_argument("--vec-per-lane", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the launch-shape autotuner (runs before the timed region)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

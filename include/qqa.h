@@ -176,6 +176,20 @@ int qqa_run_create(qqa_problem *const *problems, const qqa_params *params, int32
 void qqa_run_destroy(qqa_run *r);
 /* Layout actually used (after auto choices). */
 int qqa_run_config(const qqa_run *r, qqa_launch_config *out);
+/*
+ * Autotuner: time candidate launch shapes of the fused step on a temporary
+ * run of these instances and return the fastest in *out (*best_us_per_step
+ * receives its time per step, may be NULL). Candidates: kernel (direct,
+ * stream with 4 or 8 prefetched neighbours, staged with 2 or 4 row groups per
+ * warp) x lanes per row x vectors per lane covering the largest S (at most
+ * twice over) x block size. Each candidate runs a 50-step warm-up and then
+ * `trial_steps` timed steps (CUDA events on `stream`). The result is cached
+ * per (precision, S_max, kinds, count, node and edge totals) for the process.
+ * Shapes reduce the per-node replica statistics in different orders, so keep
+ * the returned shape for reproducible trajectories. Synchronises.
+ */
+int qqa_autotune(qqa_problem *const *problems, const qqa_params *params, int32_t count, int32_t trial_steps,
+                 const qqa_allocator *alloc, void *stream, qqa_launch_config *out, float *best_us_per_step);
 
 /*
  * Advance every active, unfinished instance by up to `nsteps` annealing steps
@@ -249,6 +263,60 @@ int qqa_run_set_state(qqa_run *r, int32_t slot, void *stream, const float *X, co
  * `slot` (all terms, before AdamW) to host grad[n][S]. Synchronises.
  */
 int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
+
+/* ---------------------------------------------------------- serving */
+/*
+ * Continuous-batching solve server. Requests (a host CSR graph plus its
+ * qqa_params) are queued on submit and admitted in FIFO order while the HBM
+ * budget and a free slot of the request's replica class allow (class = S
+ * rounded up to a power of two, >= 8; one run with a fixed launch shape and
+ * its own stream per class). Each qqa_server_pump admits, advances every
+ * class by `chunk_steps` annealing steps (the classes overlap on the device;
+ * requests of a class share every step launch), evaluates, and retires the
+ * requests that reached their own step count, freeing their slot and memory.
+ * Requests therefore join and leave batches between chunks. A request's
+ * results do not depend on what else is in flight (fixed shape per class).
+ * Times are host steady-clock seconds. Not thread-safe: one thread drives a
+ * server.
+ */
+#define QQA_REQ_QUEUED 0
+#define QQA_REQ_RUNNING 1
+#define QQA_REQ_DONE 2
+#define QQA_REQ_FAILED 3
+#define QQA_REQ_CANCELLED 4
+typedef struct qqa_server qqa_server;
+typedef struct qqa_request_info {
+    int32_t state;      /* QQA_REQ_* */
+    int32_t error;      /* QQA_OK or the code that failed the request (e.g. QQA_ENOMEM) */
+    int32_t S, n;
+    int32_t best_s;     /* best feasible replica of the final rounding, -1 if none */
+    int32_t feasible;   /* feasible replicas in the final rounding */
+    int64_t best_obj;   /* its objective (INT64_MIN if none / not done) */
+    int64_t bytes;      /* device bytes charged to the budget */
+    double t_submit, t_admit, t_done;
+    int32_t evaluations;/* periodic roundings recorded (one per chunk) */
+    int32_t reserved;
+} qqa_request_info;
+/* Device bytes a request is charged (state, evaluation buffers, graph). */
+int64_t qqa_request_bytes(int32_t n, int64_t nnz, int32_t S, int32_t precision, int32_t weighted);
+/* chunk_steps in [1, 50]; cfg fixes the launch shape of every class (NULL = auto); alloc may be NULL. */
+int qqa_server_create(int64_t hbm_budget_bytes, int32_t chunk_steps, int32_t slots_per_class, int32_t precision,
+                      const qqa_launch_config *cfg, const qqa_allocator *alloc, qqa_server **out);
+/* Copy the host graph and params into a new queued request. A request larger
+ * than the whole budget is failed at once with QQA_ENOMEM (see poll). */
+int qqa_server_submit(qqa_server *s, int32_t kind, int32_t n, const int32_t *row_ptr, const int32_t *col,
+                      const int32_t *w, const qqa_params *prm, int64_t *request_id);
+/* One iteration: admit, one chunk of steps per class, evaluate, retire. Synchronises. */
+int qqa_server_pump(qqa_server *s, int32_t *n_running, int32_t *n_queued, int32_t *n_finished);
+/* Drop a queued or running request; its slot and memory are freed. */
+int qqa_server_cancel(qqa_server *s, int64_t request_id);
+int qqa_server_poll(const qqa_server *s, int64_t request_id, qqa_request_info *info);
+/* Final results of a finished request (any pointer may be NULL): obj/viol/
+ * feasible/energy [S], best_x [ceil(n/32)], history [evaluations]. */
+int qqa_server_result(const qqa_server *s, int64_t request_id, int64_t *obj, int64_t *viol, uint8_t *feasible,
+                      double *energy, uint32_t *best_x, int64_t *history);
+int qqa_server_stats(const qqa_server *s, int64_t *used_bytes, int32_t *classes);
+void qqa_server_destroy(qqa_server *s);
 
 /* ------------------------------------------------------ no allocation */
 /*

@@ -19,11 +19,13 @@ import numpy as np
 
 from ._lib import (  # noqa: F401
     BF16, FP32, KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
-    QQAError, check, load, qqa_allocator, qqa_launch_config, qqa_params, ALLOC_FN, FREE_FN, SIGNATURES,
+    QQAError, check, load, qqa_allocator, qqa_launch_config, qqa_params, qqa_request_info, ALLOC_FN, FREE_FN,
+    SIGNATURES, REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED,
 )
 
-__all__ = ["Problem", "Run", "anneal", "make_params", "LaunchConfig", "QQAError", "MIS", "MAXCUT", "MAXCLIQUE",
-           "FP32", "BF16", "launch_count", "torch_allocator", "stream_handle"]
+__all__ = ["Problem", "Run", "Server", "anneal", "autotune", "make_params", "LaunchConfig", "QQAError", "MIS",
+           "MAXCUT", "MAXCLIQUE", "FP32", "BF16", "launch_count", "torch_allocator", "stream_handle",
+           "request_bytes", "round_eval_noalloc"]
 
 
 def _ptr(a, ctype):
@@ -270,6 +272,19 @@ class Run:
         return g
 
 
+def autotune(problems, params, trial_steps: int = 100, stream=None, allocator=None):
+    """qqa_autotune: the fastest launch shape for these instances (cached per
+    workload signature). Returns (qqa_launch_config, microseconds per step)."""
+    ps = (qqa_params * len(problems))(*params)
+    hs = (ctypes.c_void_p * len(problems))(*[p.handle for p in problems])
+    cfg = qqa_launch_config()
+    us = ctypes.c_float()
+    check(load().qqa_autotune(hs, ps, len(problems), int(trial_steps),
+                              ctypes.byref(allocator) if allocator else None, stream_handle(stream),
+                              ctypes.byref(cfg), ctypes.byref(us)))
+    return cfg, float(us.value)
+
+
 def round_eval_noalloc(kind: int, n: int, nnz: int, row_ptr, col, w, S: int, ld: int, X, lam: float,
                        obj, viol, feasible, energy, best_s, stream=None):
     """qqa_round_eval_noalloc: evaluate a state held in caller-owned device
@@ -295,3 +310,80 @@ def anneal(problems, params, config=None, stream=None, allocator=None) -> Run:
     check(load().qqa_anneal(hs, ps, len(problems), ctypes.byref(config) if config else None,
                             ctypes.byref(allocator) if allocator else None, stream_handle(stream), ctypes.byref(h)))
     return Run(h, problems, list(params), stream, allocator)
+
+
+def request_bytes(n: int, nnz: int, S: int, precision: int = FP32, weighted: bool = False) -> int:
+    """Device bytes the server charges a request (state, evaluation buffers, graph)."""
+    return int(load().qqa_request_bytes(int(n), int(nnz), int(S), int(precision), int(bool(weighted))))
+
+
+class Server:
+    """Continuous-batching solve server (qqa_server_*): FIFO admission by HBM
+    budget into per-replica-class runs, one chunk of steps per pump."""
+
+    def __init__(self, budget_bytes: int, chunk_steps: int = 50, slots_per_class: int = 64, precision: int = FP32,
+                 config=None, allocator=None):
+        h = ctypes.c_void_p()
+        self._alloc = allocator
+        check(load().qqa_server_create(int(budget_bytes), int(chunk_steps), int(slots_per_class), int(precision),
+                                       ctypes.byref(config) if config else None,
+                                       ctypes.byref(allocator) if allocator else None, ctypes.byref(h)))
+        self.handle = h
+        self.meta = {}
+
+    def submit(self, kind: int, graph, params: qqa_params) -> int:
+        rp = np.ascontiguousarray(graph.row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(graph.col, dtype=np.int32)
+        w = None if getattr(graph, "w", None) is None else np.ascontiguousarray(graph.w, dtype=np.int32)
+        rid = ctypes.c_int64()
+        check(load().qqa_server_submit(self.handle, int(kind), int(graph.n), _ptr(rp, ctypes.c_int32),
+                                       _ptr(col, ctypes.c_int32), _ptr(w, ctypes.c_int32), ctypes.byref(params),
+                                       ctypes.byref(rid)))
+        self.meta[rid.value] = (int(graph.n), int(params.S))
+        return rid.value
+
+    def pump(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(load().qqa_server_pump(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def poll(self, rid: int) -> dict:
+        info = qqa_request_info()
+        check(load().qqa_server_poll(self.handle, int(rid), ctypes.byref(info)))
+        return {f[0]: getattr(info, f[0]) for f in qqa_request_info._fields_ if f[0] != "reserved"}
+
+    def result(self, rid: int) -> dict:
+        n, S = self.meta[rid]
+        info = self.poll(rid)
+        obj = np.zeros(S, np.int64)
+        viol = np.zeros(S, np.int64)
+        feas = np.zeros(S, np.uint8)
+        en = np.zeros(S, np.float64)
+        bx = np.zeros((n + 31) // 32, np.uint32)
+        hist = np.zeros(max(info["evaluations"], 1), np.int64)
+        check(load().qqa_server_result(self.handle, int(rid), _ptr(obj, ctypes.c_int64), _ptr(viol, ctypes.c_int64),
+                                       _ptr(feas, ctypes.c_uint8), _ptr(en, ctypes.c_double),
+                                       _ptr(bx, ctypes.c_uint32), _ptr(hist, ctypes.c_int64)))
+        return {"obj": obj, "viol": viol, "feasible": feas.astype(bool), "energy": en, "best": info["best_s"],
+                "best_x": np.unpackbits(bx.view(np.uint8), bitorder="little")[:n].astype(np.uint8),
+                "history": hist[:info["evaluations"]], "info": info}
+
+    def cancel(self, rid: int):
+        check(load().qqa_server_cancel(self.handle, int(rid)))
+
+    def stats(self):
+        used = ctypes.c_int64()
+        classes = ctypes.c_int32()
+        check(load().qqa_server_stats(self.handle, ctypes.byref(used), ctypes.byref(classes)))
+        return used.value, classes.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qqa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

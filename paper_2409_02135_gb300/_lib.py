@@ -45,6 +45,15 @@ class qqa_launch_config(ctypes.Structure):
                 ("kernel_param", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class qqa_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("S", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("best_s", ctypes.c_int32), ("feasible", ctypes.c_int32), ("best_obj", ctypes.c_int64),
+                ("bytes", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("evaluations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -83,6 +92,7 @@ SIGNATURES = {
     "qqa_run_create": (ctypes.c_int, [_PP, _PPARAMS, _I32, _PCFG, _PALLOC, _P, _PP]),
     "qqa_run_destroy": (None, [_P]),
     "qqa_run_config": (ctypes.c_int, [_P, _PCFG]),
+    "qqa_autotune": (ctypes.c_int, [_PP, _PPARAMS, _I32, _I32, _PALLOC, _P, _PCFG, _PF]),
     "qqa_run_steps": (ctypes.c_int, [_P, _I32, _P]),
     "qqa_run_eval": (ctypes.c_int, [_P, _P]),
     "qqa_run_sync": (ctypes.c_int, [_P, _P]),
@@ -97,6 +107,15 @@ SIGNATURES = {
     "qqa_round_eval_noalloc": (ctypes.c_int, [_I32, _I32, ctypes.c_int64, _P, _P, _P, _I32, ctypes.c_int64, _P,
                                               ctypes.c_float, _P, _P, _P, _P, _P, _P]),
     "qqa_noalloc_last_error": (ctypes.c_char_p, []),
+    "qqa_request_bytes": (ctypes.c_int64, [_I32, ctypes.c_int64, _I32, _I32, _I32]),
+    "qqa_server_create": (ctypes.c_int, [ctypes.c_int64, _I32, _I32, _I32, _PCFG, _PALLOC, _PP]),
+    "qqa_server_submit": (ctypes.c_int, [_P, _I32, _I32, _PI32, _PI32, _PI32, _PPARAMS, _PI64]),
+    "qqa_server_pump": (ctypes.c_int, [_P, _PI32, _PI32, _PI32]),
+    "qqa_server_cancel": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "qqa_server_poll": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(qqa_request_info)]),
+    "qqa_server_result": (ctypes.c_int, [_P, ctypes.c_int64, _PI64, _PI64, _PU8, _PD, _PU32, _PI64]),
+    "qqa_server_stats": (ctypes.c_int, [_P, _PI64, _PI32]),
+    "qqa_server_destroy": (None, [_P]),
 }
 
 _lib = None

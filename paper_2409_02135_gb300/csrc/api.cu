@@ -239,6 +239,7 @@ struct qqa_run {
     qqa_launch_config cfg{};
     int32_t rows_per_tile = 0, max_grid = 0, smem = 0;
     StepFn step_fn = nullptr;
+    bool dynamic = false;             // slots come and go: always launch the full persistent grid
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
     int32_t chunk_rows = 0, buf_elems = 0;
     Alloc alloc;
@@ -412,7 +413,9 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
 extern "C" int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
                                     const qqa_allocator *alloc, void *stream, qqa_run **out)
 {
-    return run_create_hinted(capacity, S_max, precision, cfg, alloc, stream, 0, out);
+    const int rc = run_create_hinted(capacity, S_max, precision, cfg, alloc, stream, 0, out);
+    if (!rc) (*out)->dynamic = true;
+    return rc;
 }
 
 static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
@@ -585,7 +588,16 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     }
     QQA_CK_LAUNCH("init");
     rc = rebuild_tiles(r, st);
-    if (rc) return rc;
+    if (rc) {   // no room for the grown tile list: undo the add, keep the other slots running
+        const std::string msg = g_last_error;
+        r->h_descs[k].active = 0;
+        s.active = false;
+        (void)upload_desc(r, k, st);
+        cudaStreamSynchronize(st);
+        free_slot(r, k, st);
+        (void)rebuild_tiles(r, st);
+        return fail(rc, "%s", msg.c_str());
+    }
     if (slot_out) *slot_out = k;
     return QQA_OK;
 }
@@ -749,11 +761,11 @@ extern "C" int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream)
     if (nsteps < 0) return fail(QQA_EINVAL, "nsteps < 0");
     if (nsteps == 0 || r->num_tiles == 0) return QQA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int32_t grid = std::min(r->max_grid, r->num_tiles);
+    const int32_t grid = r->dynamic ? r->max_grid : std::min(r->max_grid, r->num_tiles);
     int32_t left = nsteps;
     while (left > 0) {
         const int32_t chunk = std::min(left, kGraphChunk);
-        if (r->cfg.use_graphs && chunk == kGraphChunk) {
+        if (r->cfg.use_graphs) {
             cudaGraphExec_t ge = nullptr;
             int rc = get_graph(r, chunk, grid, &ge);
             if (rc) return rc;

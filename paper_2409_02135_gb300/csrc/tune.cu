@@ -1,0 +1,112 @@
+// tune.cu -- autotuner for the launch shape of the fused step kernel.
+//
+// The shape choices are the kernel variant (direct gather, cp.async stream
+// with 4 or 8 prefetched neighbours, TMA-staged with 2 or 4 row groups per
+// warp), the lanes per node row G and 16-byte vectors per lane VPL that cover
+// S_max replicas, and the block size. Each candidate runs on a temporary run
+// of the caller's instances: one warm-up chunk, then `trial_steps` steps timed
+// with CUDA events on the caller's stream. The fastest shape is returned and
+// cached for the process, keyed by (precision, S_max, kinds, node and edge
+// totals). Different shapes reduce the replica statistics in different orders,
+// so a caller that needs reproducible trajectories keeps the shape it got.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qqa.h"
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<qqa_launch_config, float>> g_tune_cache;
+
+std::string signature(qqa_problem *const *problems, const qqa_params *params, int32_t count)
+{
+    long long n = 0, nnz = 0;
+    int32_t S_max = 0, kinds = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        int32_t kind = 0, nk = 0;
+        int64_t z = 0;
+        qqa_problem_info(problems[k], &kind, &nk, &z);
+        n += nk;
+        nnz += z;
+        kinds |= 1 << kind;
+        if (params[k].S > S_max) S_max = params[k].S;
+    }
+    char buf[160];
+    snprintf(buf, sizeof buf, "p%d|S%d|k%d|c%d|n%lld|z%lld", params[0].precision, S_max, kinds, count, n, nnz);
+    return buf;
+}
+
+}  // namespace
+
+extern "C" int qqa_autotune(qqa_problem *const *problems, const qqa_params *params, int32_t count,
+                            int32_t trial_steps, const qqa_allocator *alloc, void *stream, qqa_launch_config *out,
+                            float *best_us_per_step)
+{
+    if (!problems || !params || count < 1 || !out) return QQA_EINVAL;
+    if (trial_steps < 1) trial_steps = 100;
+    const std::string key = signature(problems, params, count);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *out = it->second.first;
+            if (best_us_per_step) *best_us_per_step = it->second.second;
+            return QQA_OK;
+        }
+    }
+    int32_t S_max = 1;
+    for (int32_t k = 0; k < count; ++k) S_max = params[k].S > S_max ? params[k].S : S_max;
+    const int vec = params[0].precision == QQA_FP32 ? 4 : 8;
+    const int nvec = (S_max + vec - 1) / vec;
+
+    std::vector<qqa_launch_config> cands;
+    for (int G = 1; G <= 32; G *= 2)
+        for (int VPL = 1; VPL <= 8; VPL *= 2) {
+            if (G * VPL < nvec || (G * VPL >= 2 * nvec && G * VPL > 1)) continue;   // cover S, at most 2x over
+            for (int bt : {0, 128, 256}) cands.push_back(qqa_launch_config{G, VPL, bt, 0, 1, QQA_KERNEL_DIRECT, 0, 0});
+            for (int nb : {4, 8}) cands.push_back(qqa_launch_config{G, VPL, 256, 0, 1, QQA_KERNEL_STREAM, nb, 0});
+            for (int rpw : {2, 4}) cands.push_back(qqa_launch_config{G, VPL, 256, 0, 1, QQA_KERNEL_STAGED, rpw, 0});
+        }
+
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return QQA_ECUDA;
+    }
+    float best = -1.0f;
+    qqa_launch_config best_cfg{};
+    for (const qqa_launch_config &c : cands) {
+        qqa_run *r = nullptr;
+        if (qqa_run_create(problems, params, count, &c, alloc, stream, &r) != QQA_OK) continue;   // shape not built
+        float ms = -1.0f;
+        if (qqa_run_steps(r, 50, stream) == QQA_OK && cudaEventRecord(e0, st) == cudaSuccess &&
+            qqa_run_steps(r, trial_steps, stream) == QQA_OK && cudaEventRecord(e1, st) == cudaSuccess &&
+            cudaEventSynchronize(e1) == cudaSuccess)
+            cudaEventElapsedTime(&ms, e0, e1);
+        qqa_launch_config used{};
+        qqa_run_config(r, &used);
+        qqa_run_destroy(r);
+        (void)cudaGetLastError();
+        if (ms > 0.0f && (best < 0.0f || ms < best)) {
+            best = ms;
+            best_cfg = used;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0.0f) return QQA_ECUDA;
+    best_cfg.grid_blocks = 0;   // re-derived from occupancy when the run is created
+    const float us = 1000.0f * best / (float)trial_steps;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best_cfg, us};
+    }
+    *out = best_cfg;
+    if (best_us_per_step) *best_us_per_step = us;
+    return QQA_OK;
+}

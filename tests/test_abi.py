@@ -80,3 +80,16 @@ def test_run_create_rejects_bad_arguments(lib):
     assert lib.qqa_run_create_empty(0, 8, 0, None, None, None, ctypes.byref(h)) == -1
     assert lib.qqa_run_create_empty(4, 5000, 0, None, None, None, ctypes.byref(h)) == -1
     assert lib.qqa_run_create_empty(4, 8, 3, None, None, None, ctypes.byref(h)) == -1
+
+
+def test_request_bytes_accounting(lib):
+    """Budget accounting of the server: state (FP32: X twice, m, v = 16 B per
+    padded element; BF16: 12 B), evaluation buffers and the CSR."""
+    import paper_2409_02135_gb300 as qqa
+    n, nnz, S = 1000, 8000, 100
+    elems = n * 100
+    fp32 = qqa.request_bytes(n, nnz, S, qqa.FP32)
+    assert fp32 == elems * 16 + n * 4 * 4 + 100 * 56 + 32 * 4 + 4096 + 4 * (n + 1) + 4 * nnz
+    bf16 = qqa.request_bytes(n, nnz, S, qqa.BF16, weighted=True)
+    elems16 = n * 104
+    assert bf16 == elems16 * 12 + n * 4 * 4 + 104 * 56 + 32 * 4 + 4096 + 4 * (n + 1) + 8 * nnz

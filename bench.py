@@ -188,6 +188,34 @@ def sum_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+# ------------------------------------------------------------ time to quality
+def time_to_quality(workload: str, run, count: int, anneal_start, chunk_events, R: int):
+    """Seconds from the start of the last timed anneal until each instance's
+    best feasible objective (periodic rounding after every chunk) first reaches
+    99% of the oracle's mean final best (tests/golden/oracle_quality_*.json)."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_quality_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    ref = json.load(open(path))["instances"]
+    times, reached = [], 0
+    for j in range(min(count, len(ref))):
+        target = ref[j]["oracle_mean_best"]
+        hist, at = run.history(j)
+        t_hit = None
+        for e, (best, step) in enumerate(zip(hist, at)):
+            if best > -(2 ** 62) and best >= 0.99 * target and e < len(chunk_events):
+                t_hit = anneal_start.elapsed_time(chunk_events[e][1]) / 1000.0
+                break
+        if t_hit is not None:
+            reached += 1
+            times.append(t_hit)
+    if not times:
+        return {"reached": 0, "instances": min(count, len(ref))}
+    times.sort()
+    return {"median_s": times[len(times) // 2], "max_s": times[-1], "reached": reached,
+            "instances": min(count, len(ref)), "target": "0.99 x oracle mean final best (4 seeds)"}
+
+
 # ----------------------------------------------------------------- oracle leg
 def oracle_sample(wl, budget_steps: int):
     """The FP64 oracle on a bounded sample: the first instance, the first
@@ -356,6 +384,33 @@ def run_ours(args):
     for j in range(len(probs)):
         r = run.result(j, with_x=False)
         quality.append(int(r["obj"][r["best"]]) if r["best"] >= 0 else None)
+    ttq = time_to_quality(args.workload, run, len(probs), step_ev[-1][0], chunk_ev[-1], R)
+
+    plain = None
+    if not args.no_plain and len(probs) > 1 and world == 1:
+        # every instance alone (one run per instance, same launch shape), one after another
+        runs1 = [qqa.Run.create([pb], [pr], config=cfg, stream=stream, allocator=alloc) for pb, pr in zip(probs, params)]
+        for r1 in runs1:
+            r1.reset(40_000)
+            for c in range(chunks):
+                r1.steps(min(R, K - c * R))
+                r1.eval()
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r1 in runs1:
+            r1.reset(50_000)
+            for c in range(chunks):
+                r1.steps(min(R, K - c * R))
+                r1.eval()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_s = e0.elapsed_time(e1) / 1000.0
+        plain = {"value": replica_steps / plain_s, "unit": METRIC, "ms_per_step": 1000 * plain_s,
+                 "batched_over_plain": (replica_steps / (statistics.mean(ms) / 1000.0)) / (replica_steps / plain_s)}
+        for r1 in runs1:
+            r1.close()
 
     prec = wl.instances[0].params.precision
     line = {
@@ -376,12 +431,81 @@ def run_ours(args):
         "replica_node_updates_per_s": sum_over_ranks(sum(i.graph.n * i.params.S * i.params.steps
                                                          for i in wl.instances) * args.steps, world) / dev_s_max,
         "wall_s_timed_region": wall, "best_objective_per_instance": quality,
+        "time_to_oracle_quality": ttq, "plain": plain,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args):
+    """Poisson trace of MIS / max-cut requests through the continuous-batching
+    server; latency from arrival to retirement (host clock), throughput in
+    completed replica-steps per second. Graphs are generated before the clock
+    starts; each request's CSR is submitted (copied) at its arrival time."""
+    import torch
+    import paper_2409_02135_gb300 as qqa
+    from paper_2409_02135_gb300 import _build
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    _build.build()
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    trace = W.serving_trace(num=args.serve_requests, rate_per_s=args.serve_rate, seed=9 + rank)
+    graphs = [W.graph_from_spec(spec) for _, spec, _ in trace]
+
+    def play(rate_scale: float):
+        srv = qqa.Server(64 << 30, chunk_steps=50, slots_per_class=64, precision=W.BF16)
+        arrivals = [a / rate_scale for a, _, _ in trace]
+        ids = {}
+        nxt = 0
+        launches0 = qqa.launch_count()
+        t0 = time.perf_counter()
+        done = 0
+        while done < len(trace):
+            now = time.perf_counter() - t0
+            while nxt < len(trace) and arrivals[nxt] <= now:
+                spec, p = trace[nxt][1], trace[nxt][2]
+                ids[nxt] = (srv.submit(spec[0], graphs[nxt], qqa.make_params(p)), t0 + arrivals[nxt])
+                nxt += 1
+            running, queued, _ = srv.pump() if ids else (0, 0, 0)
+            done = sum(1 for rid, _ in ids.values() if srv.poll(rid)["state"] >= qqa.REQ_DONE)
+            if running == 0 and queued == 0 and nxt < len(trace):
+                time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
+        wall = time.perf_counter() - t0
+        lat, rs, ok = [], 0, 0
+        for k, (rid, t_arr) in ids.items():
+            info = srv.poll(rid)
+            lat.append(info["t_done"] - t_arr)
+            if info["state"] == qqa.REQ_DONE:
+                ok += 1
+                rs += trace[k][2].S * trace[k][2].steps
+        srv.close()
+        lat.sort()
+        return {"rate_per_s": args.serve_rate * rate_scale, "requests": len(trace), "completed": ok,
+                "wall_s": wall, "value": rs / wall, "p50_s": lat[len(lat) // 2],
+                "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "gpu_launches": qqa.launch_count() - launches0}
+
+    with ClockSampler(local) as clocks:
+        full = play(1.0)
+        # capacity: completed requests per second with the queue always full
+        capacity = full["completed"] / full["wall_s"]
+        light = play(0.7 * capacity / args.serve_rate)
+    line = {"metric": METRIC, "value": full["value"], "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": 1000 * full["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-storage/f32-math", "data": "synthetic",
+            "config": {"workload": f"serving_poisson{int(args.serve_rate)}_x{len(trace)}",
+                       "requests": "MIS/max-cut, ER avg degree 10, n log-uniform [1e3, 1e6], S in {32..256}, "
+                                   "steps U[1000, 5000]", "budget_bytes": 64 << 30, "chunk_steps": 50},
+            "at_rate": full, "at_0.7x_capacity": light, "clocks": clocks.summary(),
+            "gpu_launches": full["gpu_launches"] + light["gpu_launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -392,7 +516,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mis_er700_800",
-                    choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512"])
+                    choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512",
+                             "serving"])
     ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream"], default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
@@ -403,12 +528,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-instance-at-a-time comparison")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    return run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_serving(args) if args.workload == "serving" else run_ours(args)
 
 
 if __name__ == "__main__":

@@ -283,7 +283,7 @@ def run_ours(args):
     kinds = [inst.kind for inst in wl.instances]
     probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
     params = [qqa.make_params(inst.params) for inst in wl.instances]
-    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3}[args.kernel],
+    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3, "dense": 4}[args.kernel],
                            kernel_param=args.kernel_param, group_lanes=args.group_lanes,
                            vec_per_lane=args.vec_per_lane, block_threads=args.block_threads)
     tuned_us = None
@@ -421,7 +421,7 @@ def run_ours(args):
                    "anneal_steps": K, "round_every": R, "precision": "fp32" if prec == W.FP32 else "bf16",
                    "l2": "flushed between timed anneals (512 MB write)",
                    "parallelism": f"instances x{world} ranks" if world > 1 else "single GPU",
-                   "launch": {"kernel": ["auto", "direct", "staged", "stream"][run.config().kernel],
+                   "launch": {"kernel": ["auto", "direct", "staged", "stream", "dense"][run.config().kernel],
                               "group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
                               "kernel_param": run.config().kernel_param,
                               "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--workload", default="mis_er700_800",
                     choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512",
                              "serving"])
-    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense"], default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
     ap.add_argument("--vec-per-lane", type=int, default=0)

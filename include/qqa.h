@@ -96,13 +96,21 @@ typedef struct qqa_params {
  *                 QQA_KERNEL_STREAM (each thread prefetches the next row's
  *                 slices with cp.async into private shared memory; for
  *                 sparse, memory-bound graphs)
+ *                 QQA_KERNEL_DENSE (FP32 runs, S <= 256, dense graphs: the
+ *                 product A.p runs on the tensor cores - tcgen05.mma on an
+ *                 fp16 adjacency and two fp16 planes of p, FP32 accumulation
+ *                 in tensor memory - fused with the rest of the step; needs
+ *                 an n_pad^2 fp16 adjacency per instance, n_pad = n rounded
+ *                 up to 128; edge weights must be exact in fp16, |w| <= 2048)
  *   kernel_param: staged: row groups per warp (2, 4, 8);
- *                 stream: neighbour rows prefetched per row (4, 8)
+ *                 stream: neighbour rows prefetched per row (4, 8);
+ *                 dense: reported MMA width (64, 128, 256)
  */
 #define QQA_KERNEL_AUTO 0
 #define QQA_KERNEL_DIRECT 1
 #define QQA_KERNEL_STAGED 2
 #define QQA_KERNEL_STREAM 3
+#define QQA_KERNEL_DENSE 4
 typedef struct qqa_launch_config {
     int32_t group_lanes;
     int32_t vec_per_lane;

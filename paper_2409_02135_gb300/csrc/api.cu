@@ -18,6 +18,9 @@
 #include <atomic>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/qqa.h"
 #include "qqa_internal.cuh"
 
@@ -30,6 +33,9 @@ TiledFn step_tiled_kernel_fp32(int G, int VPL, int RPW);
 TiledFn step_tiled_kernel_bf16(int G, int VPL, int RPW);
 StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
 StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
+StepFn step_dense_kernel_fp32(int N);
+int dense_threads();
+int dense_smem_bytes(int N);
 }  // namespace qqa
 
 using namespace qqa;
@@ -96,6 +102,7 @@ struct Alloc {
 struct qqa_problem {
     int32_t kind = 0, n = 0;
     int64_t nnz = 0;
+    int32_t max_abs_w = 1;   // largest |edge weight| (1 when unweighted)
     int32_t *row_ptr = nullptr, *col = nullptr, *w = nullptr;
     Alloc alloc;
 };
@@ -177,6 +184,8 @@ extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_pt
     p->kind = kind;
     p->n = n;
     p->nnz = row_ptr[n];
+    if (w)
+        for (int64_t k = 0; k < p->nnz; ++k) p->max_abs_w = std::max(p->max_abs_w, w[k] < 0 ? -w[k] : w[k]);
     p->alloc = Alloc::from(alloc);
     p->row_ptr = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)(n + 1), st);
     p->col = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
@@ -240,6 +249,7 @@ struct qqa_run {
     int32_t rows_per_tile = 0, max_grid = 0, smem = 0;
     StepFn step_fn = nullptr;
     bool dynamic = false;             // slots come and go: always launch the full persistent grid
+    int32_t dense_N = 0;              // > 0: tensor-core step (MMA width = replicas covered)
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
     int32_t chunk_rows = 0, buf_elems = 0;
     Alloc alloc;
@@ -293,7 +303,34 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     int mode = c.kernel;
     if (mode == QQA_KERNEL_AUTO)
         mode = (staged_hint && (c.block_threads == 0 || c.block_threads == 256)) ? QQA_KERNEL_STAGED : QQA_KERNEL_DIRECT;
-    if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_STREAM) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
+    if (mode == QQA_KERNEL_AUTO) mode = QQA_KERNEL_DIRECT;
+    if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_DENSE) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
+    if (mode == QQA_KERNEL_DENSE) {
+        if (r->prec != kFP32) return fail(QQA_EINVAL, "the dense tensor-core step needs an FP32 run");
+        const int N = r->S_max_pad <= 64 ? 64 : (r->S_max_pad <= 128 ? 128 : (r->S_max_pad <= 256 ? 256 : 0));
+        if (!N) return fail(QQA_EINVAL, "the dense tensor-core step covers at most 256 replicas");
+        r->step_fn = step_dense_kernel_fp32(N);
+        r->tiled_fn = nullptr;
+        r->dense_N = N;
+        r->smem = dense_smem_bytes(N);
+        const int block_d = dense_threads();
+        int dev = 0, sms = 0, occ = 0;
+        QQA_CK(cudaGetDevice(&dev));
+        QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        QQA_CK(cudaFuncSetAttribute(r->step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block_d, r->smem));
+        if (occ < 1) return fail(QQA_EINVAL, "dense step kernel does not fit on an SM");
+        r->rows_per_tile = 128;
+        c.group_lanes = 32;
+        c.vec_per_lane = 1;
+        c.block_threads = block_d;
+        c.kernel = mode;
+        c.kernel_param = N;
+        r->max_grid = c.grid_blocks ? c.grid_blocks : sms * occ;
+        c.grid_blocks = r->max_grid;
+        r->cfg = c;
+        return QQA_OK;
+    }
     int rpw = c.kernel_param ? c.kernel_param : (mode == QQA_KERNEL_STREAM ? 8 : 4);
     if (mode == QQA_KERNEL_STAGED) {
         r->tiled_fn = r->prec == kFP32 ? step_tiled_kernel_fp32(G, VPL, rpw) : step_tiled_kernel_bf16(G, VPL, rpw);
@@ -480,6 +517,63 @@ static int check_params(const qqa_params *p, int32_t S_max, int32_t prec)
     return QQA_OK;
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// Adjacency in fp16, state planes, and the five TMA tensor maps of a dense slot.
+static int setup_dense_slot(qqa_run *r, int32_t k, InstDesc &d, std::vector<void *> &dev, cudaStream_t st)
+{
+    const int N = r->dense_N;
+    const int64_t n_pad = (d.n + 127) / 128 * 128;
+    const size_t a_bytes = (size_t)n_pad * n_pad * 2, x_bytes = (size_t)4 * N * n_pad * 2;
+    d.n_pad = (int32_t)n_pad;
+    d.dense_N = N;
+    d.dense_A = (uint16_t *)r->alloc.get(a_bytes, st);
+    d.dense_XT = (uint16_t *)r->alloc.get(x_bytes, st);
+    void *tm = r->alloc.get(5 * sizeof(CUtensorMap), st);
+    if (d.dense_A) dev.push_back(d.dense_A);
+    if (d.dense_XT) dev.push_back(d.dense_XT);
+    if (tm) dev.push_back(tm);
+    if (!d.dense_A || !d.dense_XT || !tm) return fail(QQA_ENOMEM, "dense adjacency of %lld x %lld fp16 does not fit",
+                                                     (long long)n_pad, (long long)n_pad);
+    d.dense_tmaps = tm;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(QQA_ECUDA, "cuTensorMapEncodeTiled is not available");
+    alignas(64) CUtensorMap maps[5];
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint64_t adims[2] = {(cuuint64_t)n_pad, (cuuint64_t)n_pad}, astr[1] = {(cuuint64_t)n_pad * 2};
+    const cuuint32_t abox[2] = {64, 128};
+    CUresult cr = enc(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, d.dense_A, adims, astr, abox, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t xdims[2] = {(cuuint64_t)n_pad, (cuuint64_t)N}, xstr[1] = {(cuuint64_t)n_pad * 2};
+    const cuuint32_t xbox[2] = {64, (cuuint32_t)N};
+    for (int p = 0; p < 4 && cr == CUDA_SUCCESS; ++p)
+        cr = enc(&maps[1 + p], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, d.dense_XT + (size_t)p * N * n_pad, xdims, xstr,
+                 xbox, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return fail(QQA_ECUDA, "tensor map encoding failed (%d)", (int)cr);
+    QQA_CK(cudaMemsetAsync(d.dense_A, 0, a_bytes, st));
+    QQA_CK(cudaMemsetAsync(d.dense_XT, 0, x_bytes, st));
+    QQA_CK(cudaMemcpyAsync(tm, maps, sizeof maps, cudaMemcpyHostToDevice, st));
+    QQA_CK(cudaStreamSynchronize(st));
+    (void)k;
+    return QQA_OK;
+}
+
 static void free_slot(qqa_run *r, int32_t k, cudaStream_t st)
 {
     SlotHost &s = r->slots[k];
@@ -545,6 +639,19 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
         free_slot(r, k, st);
         return fail(QQA_ENOMEM, "device allocation for instance state failed (n=%d, S=%d)", s.n, s.S);
     }
+    if (r->dense_N) {
+        if (prob->max_abs_w > 2048) {
+            free_slot(r, k, st);
+            return fail(QQA_EINVAL, "edge weights above 2048 are not exact in the fp16 adjacency of the dense step");
+        }
+        d.n = s.n;
+        const int drc = setup_dense_slot(r, k, d, s.dev, st);
+        if (drc) {
+            const std::string msg = g_last_error;
+            free_slot(r, k, st);
+            return fail(drc, "%s", msg.c_str());
+        }
+    }
     d.n = s.n;
     d.S = s.S;
     d.S_pad = s.S_pad;
@@ -585,6 +692,11 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     if (prob->kind == QQA_MAXCLIQUE) {
         launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
         g_launches += 1;
+    }
+    if (r->dense_N) {
+        launch_dense_adjacency(r->d_descs, k, s.n, st);
+        launch_dense_planes(r->d_descs, k, s.n, s.S_pad, st);
+        g_launches += 2;
     }
     QQA_CK_LAUNCH("init");
     rc = rebuild_tiles(r, st);
@@ -637,6 +749,10 @@ extern "C" int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stre
         g_launches += 1;
         if (s.prob->kind == QQA_MAXCLIQUE) {
             launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+            g_launches += 1;
+        }
+        if (r->dense_N) {
+            launch_dense_planes(r->d_descs, k, s.n, s.S_pad, st);
             g_launches += 1;
         }
     }
@@ -974,6 +1090,10 @@ extern "C" int qqa_run_set_state(qqa_run *r, int32_t k, void *stream, const floa
     g_launches += 1;
     if (s.prob->kind == QQA_MAXCLIQUE) {
         launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+        g_launches += 1;
+    }
+    if (r->dense_N) {
+        launch_dense_planes(r->d_descs, k, s.n, s.S_pad, st);
         g_launches += 1;
     }
     QQA_CK_LAUNCH("set_state");

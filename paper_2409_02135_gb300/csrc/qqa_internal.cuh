@@ -41,6 +41,11 @@ struct __align__(16) InstDesc {
     int32_t *hist_step;          // [hist_cap]
     float4 *scal;                // per-step scalars of the current chunk [kMaxChunk]: x = gamma_t * (-2a),
                                  // y = lr / (1 - b1^(t+1)), z = 1 / sqrt(1 - b2^(t+1))
+    // dense tensor-core path (FP32 runs of dense graphs); null otherwise
+    uint16_t *dense_A;           // fp16 adjacency [n_pad][n_pad], zero padded
+    uint16_t *dense_XT;          // fp16 state planes [2 buffers][2 (hi, lo)][dense_N][n_pad]: p^t[j][s] at [s][j]
+    const void *dense_tmaps;     // 5 TMA tensor maps: adjacency, then planes (buffer 0 hi, lo, buffer 1 hi, lo)
+    int32_t n_pad, dense_N, pad4, pad5;
     // sizes
     int32_t n, S, S_pad, W;
     int32_t kind, a_ent, t, K;
@@ -238,6 +243,9 @@ bool step_variant_exists(int32_t prec, int32_t group_lanes, int32_t vec_per_lane
 int step_max_active_blocks(int32_t prec, int32_t group_lanes, int32_t vec_per_lane, int32_t block);
 
 void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, int32_t prec, cudaStream_t st);
+// dense tensor-core path: adjacency from CSR, state planes from X[t & 1]
+void launch_dense_adjacency(const InstDesc *descs, int32_t slot, int32_t n, cudaStream_t st);
+void launch_dense_planes(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, cudaStream_t st);
 void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st);
 void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);

@@ -1,0 +1,398 @@
+// step_dense.cu -- the fused PQQA step on the 5th-generation tensor cores, for
+// dense graphs (FP32 runs).
+//
+// The sparse product of the step, Y[i][s] = sum_j A_ij p^t[j][s] (Eqs. 22, 24,
+// 26), is a dense contraction when the graph is dense (ER with p = 0.15 has
+// about 112 neighbours per 750 nodes). Here it runs as a GEMM on tcgen05:
+//   - A is kept as an fp16 adjacency [n_pad][n_pad] (0/1 or small integer
+//     weights, exact in fp16), zero padded to a multiple of 128;
+//   - p^t is kept, besides its FP32 copy, as two fp16 planes hi = fp16(p) and
+//     lo = fp16(p - hi), stored transposed ([s][j]); hi + lo carries about 22
+//     significant bits, and D = A.hi + A.lo is accumulated in FP32 in tensor
+//     memory (every product is exact), so Y matches the FP32 gather to the
+//     rounding of an FP32 sum;
+//   - one CTA owns 128 rows of one instance: a control thread streams 64-wide
+//     K chunks of A and of both planes into shared memory with TMA (128-byte
+//     swizzle, 3 stages - 2 at N = 256 - mbarrier completion, bounded waits) and issues
+//     tcgen05.mma (M = 128, N = dense_N, K = 16) into a TMEM accumulator;
+//   - 16 epilogue warps read the accumulator with tcgen05.ld (TMEM lane =
+//     row, column = replica), form the row statistics over the S replicas
+//     through shared memory, and apply the gradient, AdamW, noise and clamp
+//     exactly as the other step kernels do. They write p^{t+1} in FP32 and as
+//     the two transposed fp16 planes for the next step's GEMM (one row per
+//     lane, so the plane writes are coalesced).
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include "step_impl.cuh"
+
+namespace qqa {
+
+namespace {
+
+// pipeline depth: three stages up to N = 128, two at N = 256 (80 KB per stage)
+__host__ __device__ constexpr int dense_stages(int N) { return N >= 256 ? 2 : 3; }
+constexpr int kDenseEpiWarps = 16;
+constexpr int kDenseThreads = (kDenseEpiWarps + 1) * 32;
+
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
+{
+    // K-major operand, 128-byte swizzle: start address >> 4, leading byte
+    // offset (unused for this layout) 1, stride byte offset 1024 >> 4 (eight
+    // 128-byte rows), descriptor version 1, layout type 2 (128B swizzle)
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)64 << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_limit(uint32_t mbar, uint32_t parity)
+{
+    const long long start = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - start > (1LL << 31)) return false;   // ~1 s
+    }
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kDenseEpiWarps * 32) : "memory"); }
+
+}  // namespace
+
+// N = MMA width = replicas covered (64, 128 or 256).
+template <int N>
+__global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const InstDesc *__restrict__ descs,
+                                                                          const Tile *__restrict__ tiles,
+                                                                          const int32_t *__restrict__ num_tiles_p,
+                                                                          RunStatus *__restrict__ status, int32_t r)
+{
+    constexpr int A_BYTES = 128 * 128;       // 128 rows x 64 fp16
+    constexpr int B_BYTES = N * 128;         // N rows x 64 fp16
+    constexpr int STAGE = A_BYTES + 2 * B_BYTES;
+    constexpr int CPT = N / 4;               // replica columns per epilogue thread
+    constexpr int kDenseStages = dense_stages(N);
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stages = base;
+    uint64_t *mb_full = reinterpret_cast<uint64_t *>(base + kDenseStages * STAGE);
+    uint64_t *mb_empty = mb_full + kDenseStages;
+    uint64_t *mb_acc = mb_empty + kDenseStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mb_acc + 1);
+    float *red = reinterpret_cast<float *>(tmem_slot + 4);   // [4][128] partial row sums
+    float *csum = red + 4 * 128;                              // [N] clique partial column sums
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_tiles = *num_tiles_p;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kDenseStages; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_full + k)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_empty + k)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_acc)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "n"(N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    uint32_t chunk_base = 0;   // K chunks this CTA has streamed so far (control thread)
+    uint32_t tiles_done = 0;   // accumulator phases completed (all threads)
+    bool failed = false;
+
+    for (int tile = blockIdx.x; tile < num_tiles && !failed; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        const InstDesc *__restrict__ d = descs + tl.slot;
+        const int t = d->t + r;
+        if (t >= d->K) continue;   // block-uniform
+        const int n = d->n, n_pad = d->n_pad, nK = n_pad / 64;
+
+        if (warp == kDenseEpiWarps) {
+            if (lane == 0) {
+                // ---------------- control thread: TMA + MMA pipeline ----------------
+                const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(d->dense_tmaps);
+                const CUtensorMap *tmA = tm, *tmH = tm + 1 + 2 * (t & 1), *tmL = tmH + 1;
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmH) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmL) : "memory");
+                const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+                bool ok = true;
+                auto fill = [&](int kc) {
+                    const uint32_t f = chunk_base + kc;
+                    const int st = f % kDenseStages;
+                    if (f >= kDenseStages)
+                        ok = ok && mbar_wait_limit(smem_addr(mb_empty + st), ((f / kDenseStages) - 1) & 1);
+                    if (!ok) return;
+                    unsigned char *sp = stages + st * STAGE;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb_full + st)),
+                                 "r"(STAGE)
+                                 : "memory");
+                    tma_load_2d(smem_addr(sp), tmA, 64 * kc, tl.row0, smem_addr(mb_full + st));
+                    tma_load_2d(smem_addr(sp + A_BYTES), tmH, 64 * kc, 0, smem_addr(mb_full + st));
+                    tma_load_2d(smem_addr(sp + A_BYTES + B_BYTES), tmL, 64 * kc, 0, smem_addr(mb_full + st));
+                };
+                for (int kc = 0; kc < kDenseStages && kc < nK; ++kc) fill(kc);
+                for (int kc = 0; kc < nK && ok; ++kc) {
+                    const uint32_t c = chunk_base + kc;
+                    const int st = c % kDenseStages;
+                    ok = mbar_wait_limit(smem_addr(mb_full + st), (c / kDenseStages) & 1);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_addr(stages + st * STAGE);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t ad = umma_desc_sw128(sa + ks * 32);
+                        const uint64_t bh = umma_desc_sw128(sa + A_BYTES + ks * 32);
+                        const uint64_t bl = umma_desc_sw128(sa + A_BYTES + B_BYTES + ks * 32);
+                        mma_f16(tmem, ad, bh, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+                        mma_f16(tmem, ad, bl, idesc, 1u);
+                    }
+                    mma_commit(smem_addr(mb_empty + st));   // stage free once these MMAs are done
+                    if (kc + kDenseStages < nK) fill(kc + kDenseStages);
+                }
+                chunk_base += nK;
+                if (ok) mma_commit(smem_addr(mb_acc));     // accumulator complete
+                else atomicAdd(&status->timeouts, 1ULL);
+            }
+            __syncwarp();
+        } else {
+            // ---------------- 16 epilogue warps ----------------
+            const StepCtx c = make_ctx(d, t, r);
+            const int q = warp & 3, cg = warp >> 2;
+            const int rl = 32 * q + lane;              // TMEM lane / row within the tile
+            const int row = tl.row0 + rl;
+            const bool rv = row < n;
+            const int col0 = cg * CPT;
+            const float *Xc = reinterpret_cast<const float *>(d->X[t & 1]);
+            float *Xn = reinterpret_cast<float *>(d->X[(t + 1) & 1]);
+            float *mv = reinterpret_cast<float *>(d->m);
+            float *vv = reinterpret_cast<float *>(d->v);
+            const size_t rbase = (size_t)row * c.S_pad;
+            if (c.kind == kMaxClique) {
+                for (int s2 = threadIdx.x; s2 < N; s2 += kDenseEpiWarps * 32) csum[s2] = 0.0f;
+                if (tl.row0 == 0) {
+                    float *cs_zero = d->colsum + ((t + 2) % 3) * c.S_pad;
+                    for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) cs_zero[s2] = 0.0f;
+                }
+            }
+            // row statistics over the S replicas (Eq. 10), two passes through shared memory
+            float mean = 0.0f, inv_std = 0.0f;
+            if (c.alpha != 0.0f) {
+                float part = 0.0f;
+                if (rv)
+                    for (int s2 = col0; s2 < col0 + CPT && s2 < c.S; ++s2) part += Xc[rbase + s2];
+                red[cg * 128 + rl] = part;
+                epi_sync();
+                mean = (red[rl] + red[128 + rl] + red[256 + rl] + red[384 + rl]) / (float)c.S;
+                epi_sync();
+                part = 0.0f;
+                if (rv)
+                    for (int s2 = col0; s2 < col0 + CPT && s2 < c.S; ++s2) {
+                        const float dl = Xc[rbase + s2] - mean;
+                        part = fmaf(dl, dl, part);
+                    }
+                red[cg * 128 + rl] = part;
+                epi_sync();
+                inv_std = rsqrtf((red[rl] + red[128 + rl] + red[256 + rl] + red[384 + rl]) / (float)c.S + c.comm_eps);
+            } else if (c.kind == kMaxClique) {
+                epi_sync();
+            }
+            const bool acc_ok = mbar_wait_limit(smem_addr(mb_acc), tiles_done & 1);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!acc_ok) {
+                if (threadIdx.x == 0) atomicAdd(&status->timeouts, 1ULL);
+            } else {
+                __half *XTn = reinterpret_cast<__half *>(d->dense_XT) + (size_t)((t + 1) & 1) * 2 * d->dense_N * n_pad;
+                __half *XTn_lo = XTn + (size_t)d->dense_N * n_pad;
+                float dsum = 0.0f;
+                if (c.kind == kMaxCut && rv) {
+                    // weighted degree d_i = sum_k w_k
+                    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
+                    if (d->w) for (int k = k0; k < k1; ++k) dsum += (float)__ldg(d->w + k);
+                    else dsum = (float)(k1 - k0);
+                }
+                bool bad = false;
+#pragma unroll 1
+                for (int c16 = 0; c16 < CPT; c16 += 16) {
+                    uint32_t yr[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(col0 + c16), yr);
+#pragma unroll
+                    for (int e4 = 0; e4 < 16; e4 += 4) {
+                        const int s0 = col0 + c16 + e4;
+                        if (!rv || s0 >= c.S_pad) continue;
+                        const float4 P4 = *reinterpret_cast<const float4 *>(Xc + rbase + s0);
+                        const float4 M4 = *reinterpret_cast<const float4 *>(mv + rbase + s0);
+                        const float4 V4 = *reinterpret_cast<const float4 *>(vv + rbase + s0);
+                        const float Pv[4] = {P4.x, P4.y, P4.z, P4.w};
+                        float Mv[4] = {M4.x, M4.y, M4.z, M4.w};
+                        float Vv[4] = {V4.x, V4.y, V4.z, V4.w};
+                        float xi[4], pn[4];
+                        gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)(s0 >> 2), (uint32_t)t, xi);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float p = Pv[e];
+                            const float y = __uint_as_float(yr[e4 + e]);
+                            float g;
+                            if (c.kind == kMIS) g = fmaf(c.lambda, y, -1.0f);
+                            else if (c.kind == kMaxCut) g = fmaf(2.0f, y, -dsum);
+                            else g = fmaf(c.lambda, (c.cs_cur[s0 + e] - 0.5f) - y, -1.0f);
+                            const float u = fmaf(2.0f, p, -1.0f);
+                            const float u2 = u * u;
+                            float upow = u * u2;
+                            if (c.half_pow != 1) {
+                                upow = u;
+                                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
+                            }
+                            g = fmaf(c.ent_coef, upow, g);
+                            if (c.alpha != 0.0f) g = fmaf(-c.alpha * inv_std, p - mean, g);
+                            if (c.grad_dbg) c.grad_dbg[rbase + s0 + e] = g;
+                            const float mn = fmaf(c.b1, Mv[e], (1.0f - c.b1) * g);
+                            const float vn = fmaf(c.b2, Vv[e], (1.0f - c.b2) * (g * g));
+                            const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
+                            float qv = p * c.decay;
+                            qv = fmaf(-c.step_size, __fdividef(mn, denom), qv);
+                            qv = fmaf(c.noise_scale, xi[e], qv);
+                            bad |= !(fabsf(qv) <= 3.0e38f);
+                            pn[e] = fminf(fmaxf(qv, 0.0f), 1.0f);
+                            Mv[e] = mn;
+                            Vv[e] = vn;
+                        }
+                        *reinterpret_cast<float4 *>(Xn + rbase + s0) = make_float4(pn[0], pn[1], pn[2], pn[3]);
+                        *reinterpret_cast<float4 *>(mv + rbase + s0) = make_float4(Mv[0], Mv[1], Mv[2], Mv[3]);
+                        *reinterpret_cast<float4 *>(vv + rbase + s0) = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __half hi = __float2half_rn(pn[e]);
+                            const __half lo = __float2half_rn(pn[e] - __half2float(hi));
+                            XTn[(size_t)(s0 + e) * n_pad + row] = hi;      // consecutive rows across the warp
+                            XTn_lo[(size_t)(s0 + e) * n_pad + row] = lo;
+                            if (c.kind == kMaxClique) atomicAdd(csum + s0 + e, pn[e]);
+                        }
+                    }
+                }
+                if (bad) atomicAdd(&status->nonfinite, 1ULL);
+            }
+            if (c.kind == kMaxClique) {
+                epi_sync();
+                for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) atomicAdd(c.cs_next + s2, csum[s2]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (!acc_ok) failed = true;
+        }
+        ++tiles_done;
+        __syncthreads();   // the accumulator is reused by the next tile
+        failed = __syncthreads_or(failed);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(N) : "memory");
+    }
+}
+
+using StepFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t);
+
+StepFn step_dense_kernel_fp32(int N)
+{
+    if (N == 64) return qqa_step_dense_kernel<64>;
+    if (N == 128) return qqa_step_dense_kernel<128>;
+    if (N == 256) return qqa_step_dense_kernel<256>;
+    return nullptr;
+}
+
+int dense_threads() { return kDenseThreads; }
+
+int dense_smem_bytes(int N)
+{
+    const int stage = 128 * 128 + 2 * N * 128;
+    const int ns = dense_stages(N);
+    return 1024 + ns * stage + (2 * ns + 1) * 8 + 16 + 4 * 128 * 4 + N * 4 + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Dense data of a slot: the fp16 adjacency (zeroed by the host first) and the
+// fp16 planes of the state p^t (buffer t & 1).
+// ---------------------------------------------------------------------------
+__global__ void dense_adjacency_kernel(const InstDesc *__restrict__ descs, int32_t slot)
+{
+    const InstDesc &d = descs[slot];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+        __half *row = reinterpret_cast<__half *>(d.dense_A) + (size_t)i * d.n_pad;
+        for (int k = d.row_ptr[i]; k < d.row_ptr[i + 1]; ++k)
+            row[d.col[k]] = __float2half_rn(d.w ? (float)d.w[k] : 1.0f);
+    }
+}
+
+__global__ void dense_planes_kernel(const InstDesc *__restrict__ descs, int32_t slot)
+{
+    const InstDesc &d = descs[slot];
+    const int b = d.t & 1;
+    const float *X = reinterpret_cast<const float *>(d.X[b]);
+    __half *hi = reinterpret_cast<__half *>(d.dense_XT) + (size_t)b * 2 * d.dense_N * d.n_pad;
+    __half *lo = hi + (size_t)d.dense_N * d.n_pad;
+    const long long total = (long long)d.n * d.S_pad;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % d.n), s = (int)(idx / d.n);   // consecutive threads: consecutive j
+        const float x = X[(size_t)j * d.S_pad + s];
+        const __half h = __float2half_rn(x);
+        hi[(size_t)s * d.n_pad + j] = h;
+        lo[(size_t)s * d.n_pad + j] = __float2half_rn(x - __half2float(h));
+    }
+}
+
+void launch_dense_adjacency(const InstDesc *descs, int32_t slot, int32_t n, cudaStream_t st)
+{
+    dense_adjacency_kernel<<<(n + 127) / 128, 128, 0, st>>>(descs, slot);
+}
+
+void launch_dense_planes(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, cudaStream_t st)
+{
+    const long long total = (long long)n * S_pad;
+    const int grid = (int)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+    dense_planes_kernel<<<grid > 0 ? grid : 1, 256, 0, st>>>(descs, slot);
+}
+
+}  // namespace qqa

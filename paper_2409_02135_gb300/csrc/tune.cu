@@ -2,7 +2,8 @@
 //
 // The shape choices are the kernel variant (direct gather, cp.async stream
 // with 4 or 8 prefetched neighbours, TMA-staged with 2 or 4 row groups per
-// warp), the lanes per node row G and 16-byte vectors per lane VPL that cover
+// warp, and for FP32 runs of graphs up to 8192 nodes the tensor-core step),
+// the lanes per node row G and 16-byte vectors per lane VPL that cover
 // S_max replicas, and the block size. Each candidate runs on a temporary run
 // of the caller's instances: one warm-up chunk, then `trial_steps` steps timed
 // with CUDA events on the caller's stream. The fastest shape is returned and
@@ -64,6 +65,14 @@ extern "C" int qqa_autotune(qqa_problem *const *problems, const qqa_params *para
     const int nvec = (S_max + vec - 1) / vec;
 
     std::vector<qqa_launch_config> cands;
+    int32_t n_max = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        int32_t nk = 0;
+        qqa_problem_info(problems[k], nullptr, &nk, nullptr);
+        n_max = nk > n_max ? nk : n_max;
+    }
+    if (params[0].precision == QQA_FP32 && S_max <= 256 && n_max <= 8192)   // tensor-core step (fp16 adjacency)
+        cands.push_back(qqa_launch_config{0, 0, 0, 0, 1, QQA_KERNEL_DENSE, 0, 0});
     for (int G = 1; G <= 32; G *= 2)
         for (int VPL = 1; VPL <= 8; VPL *= 2) {
             if (G * VPL < nvec || (G * VPL >= 2 * nvec && G * VPL > 1)) continue;   // cover S, at most 2x over

@@ -193,6 +193,60 @@ def test_stream_kernel_single_step_parity_sparse_graph():
     _check_step(MAXCUT, g, p, BF16, run)
 
 
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("n,p_edge,S", [(750, 0.15, 128), (300, 0.2, 64), (129, 0.3, 100), (450, 0.1, 200)])
+def test_dense_tensor_core_step_matches_oracle(kind, n, p_edge, S):
+    """tcgen05 step (fp16 adjacency, two fp16 planes of p, FP32 accumulation in
+    TMEM): single steps from the same state as the oracle, cold and warm
+    moments, ragged last tile, several K chunks, MMA widths 64/128/256."""
+    g = _graph(kind, n, p_edge if kind != MAXCLIQUE else 0.5, 60 + kind, weighted=(kind == MAXCUT))
+    p = Params(S=S, steps=300, alpha_comm=0.3, lr=1.0, seed=8, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    run = make_run(kind, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
+    c = run.config()
+    assert c.kernel == qqa.KERNEL_DENSE and c.kernel_param in (64, 128, 256)
+    _check_step(kind, g, p, FP32, run)
+    run.steps(40)
+    _check_step(kind, g, p, FP32, run)
+
+
+def test_dense_step_follows_the_direct_step_and_resumes():
+    """A short trajectory of the tensor-core step stays within FP32 rounding of
+    the direct gather (summation order differs), and set_state refreshes the
+    fp16 planes so a resumed run continues bit-exactly."""
+    g = G.erdos_renyi(700, 0.15, 3)
+    p = Params(S=128, steps=400, alpha_comm=0.1, lr=1.0, seed=4)
+    a = make_run(MIS, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
+    b = make_run(MIS, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DIRECT))
+    a.steps(5)
+    b.steps(5)
+    np.testing.assert_allclose(a.get_state(0)[0], b.get_state(0)[0], atol=2e-5)
+    a.steps(45)
+    X, m, v, t = a.get_state(0)
+    a.steps(30)
+    c = make_run(MIS, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
+    c.set_state(0, X, m, v, t)
+    c.steps(30)
+    np.testing.assert_array_equal(a.get_state(0)[0], c.get_state(0)[0])
+
+
+def test_dense_step_batch_of_uneven_instances_and_quality():
+    """Several instances of different n in one dense run; final quality of a
+    full anneal within 1% of the direct kernel's."""
+    gs = [G.erdos_renyi(n, 0.15, 700 + k) for k, n in enumerate((700, 777, 540, 800))]
+    ps = [Params(S=128, steps=600, lr=1.0, seed=k) for k in range(4)]
+    cfg_d = qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE)
+    cfg_g = qqa.LaunchConfig(kernel=qqa.KERNEL_DIRECT)
+    probs = [qqa.Problem(MIS, g) for g in gs]
+    rd = qqa.anneal(probs, [qqa.make_params(p) for p in ps], config=cfg_d)
+    rg = qqa.anneal(probs, [qqa.make_params(p) for p in ps], config=cfg_g)
+    for k in range(4):
+        a, b = rd.result(k), rg.result(k)
+        assert a["best"] >= 0 and b["best"] >= 0
+        assert abs(a["obj"][a["best"]] - b["obj"][b["best"]]) <= 1
+        o, v, f, _ = oracle.cost_of_x(MIS, gs[k], 2.0, a["best_x"])
+        assert f and o == a["obj"][a["best"]]
+
+
 def test_staged_kernel_single_step_parity_dense_graph():
     g = G.erdos_renyi(750, 0.15, 1000)
     p = Params(S=128, steps=3000, alpha_comm=0.3, seed=0)

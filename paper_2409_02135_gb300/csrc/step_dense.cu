@@ -198,17 +198,20 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
             __syncwarp();
         } else {
             // ---------------- 16 epilogue warps ----------------
+            // 1. accumulator (TMEM lane = row) -> shared buffer B[128][N + 1] in the
+            //    now idle stage area; 2. coalesced row-group update (lanes over
+            //    replicas, as in the other step kernels) reading Y from B and
+            //    writing the new p back into the same row of B; 3. the fp16 planes
+            //    of the new p written transposed from B, consecutive rows per warp.
+            constexpr int LD = N + 1;                   // padded row stride: conflict-free columns
+            constexpr int GE = N / 4 >= 32 ? 32 : N / 4;    // lanes per row in the update
+            constexpr int VE = N / 4 >= 32 ? N / 128 : 1;   // 16-byte vectors per lane
+            constexpr int RPW = 32 / GE;                  // rows per warp at a time
+            float *B = reinterpret_cast<float *>(stages);
             const StepCtx c = make_ctx(d, t, r);
             const int q = warp & 3, cg = warp >> 2;
-            const int rl = 32 * q + lane;              // TMEM lane / row within the tile
-            const int row = tl.row0 + rl;
-            const bool rv = row < n;
+            const int rl = 32 * q + lane;
             const int col0 = cg * CPT;
-            const float *Xc = reinterpret_cast<const float *>(d->X[t & 1]);
-            float *Xn = reinterpret_cast<float *>(d->X[(t + 1) & 1]);
-            float *mv = reinterpret_cast<float *>(d->m);
-            float *vv = reinterpret_cast<float *>(d->v);
-            const size_t rbase = (size_t)row * c.S_pad;
             if (c.kind == kMaxClique) {
                 for (int s2 = threadIdx.x; s2 < N; s2 += kDenseEpiWarps * 32) csum[s2] = 0.0f;
                 if (tl.row0 == 0) {
@@ -216,102 +219,60 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                     for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) cs_zero[s2] = 0.0f;
                 }
             }
-            // row statistics over the S replicas (Eq. 10), two passes through shared memory
-            float mean = 0.0f, inv_std = 0.0f;
-            if (c.alpha != 0.0f) {
-                float part = 0.0f;
-                if (rv)
-                    for (int s2 = col0; s2 < col0 + CPT && s2 < c.S; ++s2) part += Xc[rbase + s2];
-                red[cg * 128 + rl] = part;
-                epi_sync();
-                mean = (red[rl] + red[128 + rl] + red[256 + rl] + red[384 + rl]) / (float)c.S;
-                epi_sync();
-                part = 0.0f;
-                if (rv)
-                    for (int s2 = col0; s2 < col0 + CPT && s2 < c.S; ++s2) {
-                        const float dl = Xc[rbase + s2] - mean;
-                        part = fmaf(dl, dl, part);
-                    }
-                red[cg * 128 + rl] = part;
-                epi_sync();
-                inv_std = rsqrtf((red[rl] + red[128 + rl] + red[256 + rl] + red[384 + rl]) / (float)c.S + c.comm_eps);
-            } else if (c.kind == kMaxClique) {
-                epi_sync();
-            }
             const bool acc_ok = mbar_wait_limit(smem_addr(mb_acc), tiles_done & 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!acc_ok) {
                 if (threadIdx.x == 0) atomicAdd(&status->timeouts, 1ULL);
             } else {
-                __half *XTn = reinterpret_cast<__half *>(d->dense_XT) + (size_t)((t + 1) & 1) * 2 * d->dense_N * n_pad;
-                __half *XTn_lo = XTn + (size_t)d->dense_N * n_pad;
-                float dsum = 0.0f;
-                if (c.kind == kMaxCut && rv) {
-                    // weighted degree d_i = sum_k w_k
-                    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
-                    if (d->w) for (int k = k0; k < k1; ++k) dsum += (float)__ldg(d->w + k);
-                    else dsum = (float)(k1 - k0);
-                }
-                bool bad = false;
 #pragma unroll 1
                 for (int c16 = 0; c16 < CPT; c16 += 16) {
                     uint32_t yr[16];
                     tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(col0 + c16), yr);
 #pragma unroll
-                    for (int e4 = 0; e4 < 16; e4 += 4) {
-                        const int s0 = col0 + c16 + e4;
-                        if (!rv || s0 >= c.S_pad) continue;
-                        const float4 P4 = *reinterpret_cast<const float4 *>(Xc + rbase + s0);
-                        const float4 M4 = *reinterpret_cast<const float4 *>(mv + rbase + s0);
-                        const float4 V4 = *reinterpret_cast<const float4 *>(vv + rbase + s0);
-                        const float Pv[4] = {P4.x, P4.y, P4.z, P4.w};
-                        float Mv[4] = {M4.x, M4.y, M4.z, M4.w};
-                        float Vv[4] = {V4.x, V4.y, V4.z, V4.w};
-                        float xi[4], pn[4];
-                        gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)(s0 >> 2), (uint32_t)t, xi);
+                    for (int e = 0; e < 16; ++e) B[rl * LD + col0 + c16 + e] = __uint_as_float(yr[e]);
+                }
+            }
+            epi_sync();
+            if (acc_ok) {
+                const int gl = lane & (GE - 1), grp = lane / GE;
+                const unsigned gmask = (GE == 32) ? 0xffffffffu : (((1u << GE) - 1u) << (grp * GE));
+                for (int rb = warp * RPW; rb < 128; rb += kDenseEpiWarps * RPW) {
+                    const int rloc = rb + grp;
+                    const int row = tl.row0 + rloc;
+                    if (row >= n) continue;   // group-uniform
+                    float Y[VE][4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float p = Pv[e];
-                            const float y = __uint_as_float(yr[e4 + e]);
-                            float g;
-                            if (c.kind == kMIS) g = fmaf(c.lambda, y, -1.0f);
-                            else if (c.kind == kMaxCut) g = fmaf(2.0f, y, -dsum);
-                            else g = fmaf(c.lambda, (c.cs_cur[s0 + e] - 0.5f) - y, -1.0f);
-                            const float u = fmaf(2.0f, p, -1.0f);
-                            const float u2 = u * u;
-                            float upow = u * u2;
-                            if (c.half_pow != 1) {
-                                upow = u;
-                                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
-                            }
-                            g = fmaf(c.ent_coef, upow, g);
-                            if (c.alpha != 0.0f) g = fmaf(-c.alpha * inv_std, p - mean, g);
-                            if (c.grad_dbg) c.grad_dbg[rbase + s0 + e] = g;
-                            const float mn = fmaf(c.b1, Mv[e], (1.0f - c.b1) * g);
-                            const float vn = fmaf(c.b2, Vv[e], (1.0f - c.b2) * (g * g));
-                            const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
-                            float qv = p * c.decay;
-                            qv = fmaf(-c.step_size, __fdividef(mn, denom), qv);
-                            qv = fmaf(c.noise_scale, xi[e], qv);
-                            bad |= !(fabsf(qv) <= 3.0e38f);
-                            pn[e] = fminf(fmaxf(qv, 0.0f), 1.0f);
-                            Mv[e] = mn;
-                            Vv[e] = vn;
-                        }
-                        *reinterpret_cast<float4 *>(Xn + rbase + s0) = make_float4(pn[0], pn[1], pn[2], pn[3]);
-                        *reinterpret_cast<float4 *>(mv + rbase + s0) = make_float4(Mv[0], Mv[1], Mv[2], Mv[3]);
-                        *reinterpret_cast<float4 *>(vv + rbase + s0) = make_float4(Vv[0], Vv[1], Vv[2], Vv[3]);
+                    for (int v = 0; v < VE; ++v)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const __half hi = __float2half_rn(pn[e]);
-                            const __half lo = __float2half_rn(pn[e] - __half2float(hi));
-                            XTn[(size_t)(s0 + e) * n_pad + row] = hi;      // consecutive rows across the warp
-                            XTn_lo[(size_t)(s0 + e) * n_pad + row] = lo;
-                            if (c.kind == kMaxClique) atomicAdd(csum + s0 + e, pn[e]);
+                        for (int e = 0; e < 4; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * 4 + e];
+                    float dsum = 0.0f;
+                    if (c.kind == kMaxCut) {
+                        const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
+                        if (d->w) {
+                            for (int k = k0 + gl; k < k1; k += GE) dsum += (float)__ldg(d->w + k);
+                            dsum = group_sum<GE>(dsum, gmask);
+                        } else {
+                            dsum = (float)(k1 - k0);
                         }
                     }
+                    OwnRow<float, GE, VE> own;
+                    load_own<float, GE, VE>(d, c, row, gl, own);
+                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own, status, csum, B + rloc * LD);
                 }
-                if (bad) atomicAdd(&status->nonfinite, 1ULL);
+            }
+            epi_sync();
+            if (acc_ok) {
+                __half *XTn = reinterpret_cast<__half *>(d->dense_XT) + (size_t)((t + 1) & 1) * 2 * d->dense_N * n_pad;
+                __half *XTn_lo = XTn + (size_t)d->dense_N * n_pad;
+                const int j = threadIdx.x & 127;   // row within the tile: consecutive across a warp
+                const int row = tl.row0 + j;
+                if (row < n)
+                    for (int s2 = threadIdx.x >> 7; s2 < c.S_pad; s2 += kDenseEpiWarps * 32 / 128) {
+                        const float pv = B[j * LD + s2];
+                        const __half hi = __float2half_rn(pv);
+                        XTn[(size_t)s2 * n_pad + row] = hi;
+                        XTn_lo[(size_t)s2 * n_pad + row] = __float2half_rn(pv - __half2float(hi));
+                    }
             }
             if (c.kind == kMaxClique) {
                 epi_sync();

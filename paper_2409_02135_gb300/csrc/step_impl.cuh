@@ -261,7 +261,7 @@ template <typename T, int G, int VPL>
 __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
                                            unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
                                            const OwnRow<T, G, VPL> &o, RunStatus *__restrict__ status,
-                                           float *colsum_acc)
+                                           float *colsum_acc, float *pn_out = nullptr)
 {
     constexpr int VEC = VecT<T>::N;
     T *__restrict__ Xn = reinterpret_cast<T *>(d->X[(c.t + 1) & 1]);
@@ -354,6 +354,10 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
         if (c.kind == kMaxClique) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) atomicAdd(colsum_acc + off + e, pn[e]);
+        }
+        if (pn_out) {   // new values also go to a caller buffer (the tensor-core step's plane transpose)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) pn_out[off + e] = pn[e];
         }
     }
 }

@@ -112,8 +112,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
     uint64_t *mb_empty = mb_full + kDenseStages;
     uint64_t *mb_acc = mb_empty + kDenseStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mb_acc + 1);
-    float *red = reinterpret_cast<float *>(tmem_slot + 4);   // [4][128] partial row sums
+    float *red = reinterpret_cast<float *>(tmem_slot + 4);   // [4][128] scratch (unused)
     float *csum = red + 4 * 128;                              // [N] clique partial column sums
+    float2 *rstat = reinterpret_cast<float2 *>(csum + N);     // [128] row mean, 1/STD (Eq. 10)
+    float *rdeg = reinterpret_cast<float *>(rstat + 128);     // [128] weighted degree (max-cut)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_tiles = *num_tiles_p;
@@ -219,6 +221,50 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                     for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) cs_zero[s2] = 0.0f;
                 }
             }
+            const int gl = lane & (GE - 1), grp = lane / GE;
+            const unsigned gmask = (GE == 32) ? 0xffffffffu : (((1u << GE) - 1u) << (grp * GE));
+            // while the tensor cores run: row statistics of p^t and max-cut degrees
+            // (they do not depend on the product)
+            for (int rb = warp * RPW; rb < 128; rb += kDenseEpiWarps * RPW) {
+                const int rloc = rb + grp;
+                const int row = tl.row0 + rloc;
+                if (row >= n) continue;   // group-uniform
+                if (c.alpha != 0.0f) {
+                    const float *prow = reinterpret_cast<const float *>(d->X[t & 1]) + (size_t)row * c.S_pad;
+                    float sum = 0.0f, xs[VE][4];
+#pragma unroll
+                    for (int v = 0; v < VE; ++v)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int s2 = (v * GE + gl) * 4 + e;
+                            xs[v][e] = s2 < c.S ? prow[s2] : 0.0f;
+                            sum += xs[v][e];
+                        }
+                    const float mean = group_sum<GE>(sum, gmask) / (float)c.S;
+                    float sq = 0.0f;
+#pragma unroll
+                    for (int v = 0; v < VE; ++v)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if ((v * GE + gl) * 4 + e < c.S) {
+                                const float dl = xs[v][e] - mean;
+                                sq = fmaf(dl, dl, sq);
+                            }
+                    const float istd = rsqrtf(group_sum<GE>(sq, gmask) / (float)c.S + c.comm_eps);
+                    if (gl == 0) rstat[rloc] = make_float2(mean, istd);
+                }
+                if (c.kind == kMaxCut) {
+                    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
+                    float ds = 0.0f;
+                    if (d->w) {
+                        for (int k = k0 + gl; k < k1; k += GE) ds += (float)__ldg(d->w + k);
+                        ds = group_sum<GE>(ds, gmask);
+                    } else {
+                        ds = (float)(k1 - k0);
+                    }
+                    if (gl == 0) rdeg[rloc] = ds;
+                }
+            }
             const bool acc_ok = mbar_wait_limit(smem_addr(mb_acc), tiles_done & 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!acc_ok) {
@@ -234,30 +280,25 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
             }
             epi_sync();
             if (acc_ok) {
-                const int gl = lane & (GE - 1), grp = lane / GE;
-                const unsigned gmask = (GE == 32) ? 0xffffffffu : (((1u << GE) - 1u) << (grp * GE));
-                for (int rb = warp * RPW; rb < 128; rb += kDenseEpiWarps * RPW) {
+                // own rows of p, m, v are loaded one row ahead of the update
+                OwnRow<float, GE, VE> own[2];
+                int rb = warp * RPW;
+                if (tl.row0 + rb + grp < n) load_own<float, GE, VE>(d, c, tl.row0 + rb + grp, gl, own[0]);
+                for (int it = 0; rb < 128; rb += kDenseEpiWarps * RPW, ++it) {
                     const int rloc = rb + grp;
                     const int row = tl.row0 + rloc;
+                    const int nrow = row + kDenseEpiWarps * RPW;
+                    if (rb + kDenseEpiWarps * RPW < 128 && nrow < n)
+                        load_own<float, GE, VE>(d, c, nrow, gl, own[(it + 1) & 1]);
                     if (row >= n) continue;   // group-uniform
                     float Y[VE][4];
 #pragma unroll
                     for (int v = 0; v < VE; ++v)
 #pragma unroll
                         for (int e = 0; e < 4; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * 4 + e];
-                    float dsum = 0.0f;
-                    if (c.kind == kMaxCut) {
-                        const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
-                        if (d->w) {
-                            for (int k = k0 + gl; k < k1; k += GE) dsum += (float)__ldg(d->w + k);
-                            dsum = group_sum<GE>(dsum, gmask);
-                        } else {
-                            dsum = (float)(k1 - k0);
-                        }
-                    }
-                    OwnRow<float, GE, VE> own;
-                    load_own<float, GE, VE>(d, c, row, gl, own);
-                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own, status, csum, B + rloc * LD);
+                    const float dsum = c.kind == kMaxCut ? rdeg[rloc] : 0.0f;
+                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, csum,
+                                              B + rloc * LD, &rstat[rloc]);
                 }
             }
             epi_sync();
@@ -309,7 +350,7 @@ int dense_smem_bytes(int N)
 {
     const int stage = 128 * 128 + 2 * N * 128;
     const int ns = dense_stages(N);
-    return 1024 + ns * stage + (2 * ns + 1) * 8 + 16 + 4 * 128 * 4 + N * 4 + 64;
+    return 1024 + ns * stage + (2 * ns + 1) * 8 + 16 + 4 * 128 * 4 + N * 4 + 128 * 8 + 128 * 4 + 64;
 }
 
 // ---------------------------------------------------------------------------

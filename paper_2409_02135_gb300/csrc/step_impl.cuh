@@ -261,7 +261,8 @@ template <typename T, int G, int VPL>
 __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
                                            unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
                                            const OwnRow<T, G, VPL> &o, RunStatus *__restrict__ status,
-                                           float *colsum_acc, float *pn_out = nullptr)
+                                           float *colsum_acc, float *pn_out = nullptr,
+                                           const float2 *pre_stats = nullptr)
 {
     constexpr int VEC = VecT<T>::N;
     T *__restrict__ Xn = reinterpret_cast<T *>(d->X[(c.t + 1) & 1]);
@@ -269,7 +270,10 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
 
     // row statistics over the S replicas (Eq. 10)
     float mean = 0.0f, inv_std = 0.0f;
-    if (c.alpha != 0.0f) {
+    if (c.alpha != 0.0f && pre_stats) {   // row statistics computed earlier by the caller
+        mean = pre_stats->x;
+        inv_std = pre_stats->y;
+    } else if (c.alpha != 0.0f) {
         float sum = 0.0f;
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {

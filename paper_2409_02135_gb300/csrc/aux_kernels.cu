@@ -130,24 +130,31 @@ __device__ __forceinline__ float state_value(const InstDesc &d, size_t e, int32_
     return prec == kFP32 ? reinterpret_cast<const float *>(d.X[d.t & 1])[e] : d.master[e];
 }
 
+// Evaluation work items: each step tile is split into `sub` pieces of
+// `rows_per_item` rows, so the evaluation keeps the GPU busy even when the
+// step kernel uses tall tiles.
 // bits[i][w] bit b = (p[i][32w+b] > 1/2) for 32w+b < S; zero the cost counters.
 __global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
-                                 const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t prec)
+                                 const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t sub,
+                                 int32_t rows_per_item, int32_t prec)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int num_tiles = *num_tiles_p;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-        const Tile tl = tiles[tile];
+    const int items = *num_tiles_p * sub;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const Tile tl = tiles[item / sub];
+        const int part = item % sub;
         const InstDesc &d = descs[tl.slot];
         if (!needs_eval(d)) continue;
-        if (tl.row0 == 0)
+        if (tl.row0 == 0 && part == 0)
             for (int k = threadIdx.x; k < 3 * d.S_pad; k += blockDim.x) d.counts[k] = 0ULL;
-        const int rows = min(rows_per_tile, d.n - tl.row0);
+        const int r0 = tl.row0 + part * rows_per_item;
+        const int rows = min(min(rows_per_item, tl.row0 + rows_per_tile - r0), d.n - r0);
+        if (rows <= 0) continue;
         const int pairs = rows * d.W;
         for (int pidx = warp; pidx < pairs; pidx += nwarps) {
-            const int i = tl.row0 + pidx / d.W;
+            const int i = r0 + pidx / d.W;
             const int w = pidx % d.W;
             const int s = 32 * w + lane;
             const bool x = s < d.S && state_value(d, (size_t)i * d.S_pad + s, prec) > 0.5f;
@@ -162,18 +169,21 @@ __global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, const Tile 
 // threads (threads sharing a replica split the rows), partial counts are
 // combined in shared memory, then added to the slot's counters.
 __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
-                                  const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile)
+                                  const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t sub,
+                                  int32_t rows_per_item)
 {
     extern __shared__ long long sh_cnt[];   // [3][S_pad32]
-    const int num_tiles = *num_tiles_p;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
-        const Tile tl = tiles[tile];
+    const int items = *num_tiles_p * sub;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const Tile tl = tiles[item / sub];
+        const int r0 = tl.row0 + (item % sub) * rows_per_item;
         const InstDesc &d = descs[tl.slot];
         if (!needs_eval(d)) continue;
+        const int row_end = min(min(r0 + rows_per_item, tl.row0 + rows_per_tile), d.n);
+        if (r0 >= row_end) continue;   // block-uniform
         const int S32 = (d.S + 31) & ~31;
         for (int k = threadIdx.x; k < 3 * S32; k += blockDim.x) sh_cnt[k] = 0;
         __syncthreads();
-        const int row_end = min(tl.row0 + rows_per_tile, d.n);
         const int splits = max(1, (int)blockDim.x / S32);
         for (int base = threadIdx.x; base < splits * S32; base += blockDim.x) {
             const int s = base % S32;
@@ -182,7 +192,7 @@ __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile
             const int w = s >> 5;
             const int b = s & 31;
             long long size = 0, inside = 0, cut = 0;
-            for (int i = tl.row0 + part; i < row_end; i += splits) {
+            for (int i = r0 + part; i < row_end; i += splits) {
                 const unsigned xi = (d.bits[(size_t)i * d.W + w] >> b) & 1u;
                 size += xi;
                 const int k1 = d.row_ptr[i + 1];
@@ -275,9 +285,14 @@ __global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32
 void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
                  int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st)
 {
-    eval_bits_kernel<<<grid, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile, prec);
+    const int rows_per_item = 8;
+    const int sub = (rows_per_tile + rows_per_item - 1) / rows_per_item;
+    const long long items = (long long)grid * sub;   // grid = number of tiles when launched
+    const int g = (int)(items < 65535 ? items : 65535);
+    eval_bits_kernel<<<g, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile, sub, rows_per_item, prec);
     const int S32 = (S_max_pad + 31) & ~31;
-    eval_count_kernel<<<grid, 256, 3 * S32 * sizeof(long long), st>>>(descs, tiles, num_tiles, rows_per_tile);
+    eval_count_kernel<<<g, 256, 3 * S32 * sizeof(long long), st>>>(descs, tiles, num_tiles, rows_per_tile, sub,
+                                                                   rows_per_item);
     eval_finalize_kernel<<<(capacity + 7) / 8, 256, 0, st>>>(descs, capacity);
 }
 

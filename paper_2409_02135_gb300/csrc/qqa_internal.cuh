@@ -9,6 +9,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace qqa {
@@ -103,10 +104,50 @@ __device__ __forceinline__ float bits_to_unit(uint32_t r)
     return (float)((r >> 8) + 1u) * 5.9604644775390625e-8f;
 }
 
-// sqrt(x) for x >= 0 from the hardware reciprocal square root (x = 0 -> 0).
+// Single-instruction approximations of the PTX ISA (flush-to-zero forms: the
+// step's values are never subnormal, and these skip the subnormal handling):
+// relative errors of a few ulp, far inside the single-step tolerance.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// sqrt(x) for x >= 0 (0 -> 0).
 __device__ __forceinline__ float sqrt_nonneg(float x)
 {
-    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float log2_ftz(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// -2 ln(u) for u = ((r >> 8) + 1) 2^-24 in (0, 1], the Box-Muller radius squared.
+// delta = 1 - u = ((~r) >> 8) 2^-24 and u = 1 - delta are exact. Away from u = 1
+// the hardware log2 is accurate relative to the result; close to u = 1 its
+// absolute error is not, so for delta < 2^-10 the Taylor series
+// -2 ln(1 - delta) = 2 delta + delta^2 + (2/3) delta^3 + ... is cut after two
+// terms (relative error below delta^2 / 3 < 3.2e-7).
+__device__ __forceinline__ float neg2_log_unit(uint32_t r)
+{
+    const float delta = (float)((~r) >> 8) * 5.9604644775390625e-8f;
+    const float series = fmaf(delta, delta, delta + delta);
+    const float via_log2 = -1.38629436111989061883f * log2_ftz(1.0f - delta);   // -2 ln 2 log2(u)
+    return delta < 9.765625e-4f ? series : via_log2;
 }
 
 // Four standard normals for replicas 4q..4q+3 of node i at step t (stream tag 1):
@@ -119,9 +160,9 @@ __device__ __forceinline__ void gauss4(uint32_t seed_lo, uint32_t seed_hi, uint3
     const U4 r = philox10(U4{i, q, t, 1u}, seed_lo, seed_hi);
     const float two_pi = 6.28318530717958647692f;
     float s0, c0, s1, c1;
-    const float rad0 = sqrt_nonneg(-2.0f * logf(bits_to_unit(r.x)));
+    const float rad0 = sqrt_nonneg(neg2_log_unit(r.x));
     __sincosf(two_pi * (bits_to_unit(r.y) - 0.5f), &s0, &c0);
-    const float rad1 = sqrt_nonneg(-2.0f * logf(bits_to_unit(r.z)));
+    const float rad1 = sqrt_nonneg(neg2_log_unit(r.z));
     __sincosf(two_pi * (bits_to_unit(r.w) - 0.5f), &s1, &c1);
     out[0] = -rad0 * c0;
     out[1] = -rad0 * s0;
@@ -167,6 +208,12 @@ struct VecT<float> {
         out[0] = __uint_as_float(a.x); out[1] = __uint_as_float(a.y);
         out[2] = __uint_as_float(a.z); out[3] = __uint_as_float(a.w);
     }
+    // y[e] += element e of a raw 16-byte vector
+    __device__ __forceinline__ static void add_to(const uint4 a, float y[4])
+    {
+        y[0] += __uint_as_float(a.x); y[1] += __uint_as_float(a.y);
+        y[2] += __uint_as_float(a.z); y[3] += __uint_as_float(a.w);
+    }
     // streaming (evict-first) variants for data touched once per step
     __device__ __forceinline__ static void load_cs(const float *p, float out[4])
     {
@@ -190,6 +237,18 @@ struct VecT<__nv_bfloat16> {
             out[2 * k] = __uint_as_float(u[k] << 16);
             out[2 * k + 1] = __uint_as_float(u[k] & 0xFFFF0000u);
         }
+    }
+    // y[e] += element e of a raw 16-byte vector, with the mixed-precision add
+    // (the BF16 operand widens exactly, so this equals unpack-then-add)
+    __device__ __forceinline__ static void add_to(const uint4 a, float y[8])
+    {
+        const uint32_t u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+                "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
+                : "+f"(y[2 * k]), "+f"(y[2 * k + 1])
+                : "r"(u[k]));
     }
     __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float out[8])
     {

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                             xs[v][e] = s2 < c.S ? prow[s2] : 0.0f;
                             sum += xs[v][e];
                         }
-                    const float mean = group_sum<GE>(sum, gmask) / (float)c.S;
+                    const float mean = group_sum<GE>(sum, gmask) * c.inv_S;
                     float sq = 0.0f;
 #pragma unroll
                     for (int v = 0; v < VE; ++v)
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                                 const float dl = xs[v][e] - mean;
                                 sq = fmaf(dl, dl, sq);
                             }
-                    const float istd = rsqrtf(group_sum<GE>(sq, gmask) / (float)c.S + c.comm_eps);
+                    const float istd = rsqrt_ftz(group_sum<GE>(sq, gmask) * c.inv_S + c.comm_eps);
                     if (gl == 0) rstat[rloc] = make_float2(mean, istd);
                 }
                 if (c.kind == kMaxCut) {

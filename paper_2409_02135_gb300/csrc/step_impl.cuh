@@ -63,11 +63,14 @@ __device__ __forceinline__ float group_sum(float x, unsigned mask)
 // once per chunk of steps (entry r = step t - t_chunk_start).
 struct StepCtx {
     int t, n, S, S_pad, kind, half_pow;
-    float ent_coef, decay, step_size, inv_sqrt_bc2, lambda, alpha, noise_scale, b1, b2, adam_eps, comm_eps;
+    float ent_coef, decay, step_size, inv_sqrt_bc2, lambda, alpha, noise_scale, b1, b2, adam_eps, comm_eps, inv_S;
     const float *cs_cur;
     float *cs_next;
     float *grad_dbg;
 };
+
+static_assert(offsetof(InstDesc, lr) % 16 == 0 && offsetof(InstDesc, comm_eps) == offsetof(InstDesc, lr) + 32,
+              "the hyper-parameters are read as three 16-byte vectors");
 
 __device__ __forceinline__ StepCtx make_ctx(const InstDesc *__restrict__ d, int t, int r)
 {
@@ -82,14 +85,18 @@ __device__ __forceinline__ StepCtx make_ctx(const InstDesc *__restrict__ d, int 
     c.step_size = sc.y;
     c.inv_sqrt_bc2 = sc.z;
     c.half_pow = (d->a_ent - 2) / 2;
-    c.decay = d->decay;
-    c.lambda = d->lambda;
-    c.alpha = d->alpha;
-    c.noise_scale = d->noise_scale;
-    c.b1 = d->b1;
-    c.b2 = d->b2;
-    c.adam_eps = d->adam_eps;
-    c.comm_eps = d->comm_eps;
+    // (lr, wd, b1, b2), (adam_eps, gmin, gmax, alpha), (comm_eps, noise_scale, lambda, decay)
+    const float4 *hp = reinterpret_cast<const float4 *>(&d->lr);
+    const float4 h0 = hp[0], h1 = hp[1], h2 = hp[2];
+    c.b1 = h0.z;
+    c.b2 = h0.w;
+    c.adam_eps = h1.x;
+    c.alpha = h1.w;
+    c.comm_eps = h2.x;
+    c.noise_scale = h2.y;
+    c.lambda = h2.z;
+    c.decay = h2.w;
+    c.inv_S = 1.0f / (float)c.S;
     c.cs_cur = nullptr;
     c.cs_next = nullptr;
     c.grad_dbg = d->grad_dbg;
@@ -184,12 +191,11 @@ __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, co
                 if (wp) dsum += w;
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) {
-                    float x[VEC];
-                    VecT<T>::unpack(raw[u][v], x);
                     if (wp == nullptr) {
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) Y[v][e] += x[e];
+                        VecT<T>::add_to(raw[u][v], Y[v]);
                     } else {
+                        float x[VEC];
+                        VecT<T>::unpack(raw[u][v], x);
 #pragma unroll
                         for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
                     }
@@ -287,7 +293,7 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
                     if (e < nv) sum += o.P[v][e];
             }
         }
-        mean = group_sum<G>(sum, gmask) / (float)c.S;
+        mean = group_sum<G>(sum, gmask) * c.inv_S;
         float sq = 0.0f;
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
@@ -298,49 +304,71 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
                 if (nv >= VEC || e < nv) sq = fmaf(dl, dl, sq);
             }
         }
-        inv_std = rsqrtf(group_sum<G>(sq, gmask) / (float)c.S + c.comm_eps);
+        inv_std = rsqrt_ftz(group_sum<G>(sq, gmask) * c.inv_S + c.comm_eps);
     }
+    // alpha = 0 gives the coefficient -0 and adds exactly nothing
+    const float comm_coef = -c.alpha * inv_std;
+    // problem gradient g = A y + B for MIS (Eq. 22) and max-cut (Eq. 26)
+    const float gA = c.kind == kMaxCut ? 2.0f : c.lambda;
+    const float gB = c.kind == kMaxCut ? -dsum : -1.0f;
+    const float om_b1 = 1.0f - c.b1, om_b2 = 1.0f - c.b2;
 
+    // The per-instance choices (problem kind, entropy exponent, gradient dump)
+    // branch once per 16-byte vector, so the element loops are straight-line.
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
         const int off = (v * G + gl) * VEC;
         if (off >= c.S_pad) continue;
+        float g[VEC];
+        if (c.kind == kMaxClique) {   // Eq. 24, column sums of the previous step
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) g[e] = fmaf(c.lambda, (c.cs_cur[off + e] - 0.5f) - Y[v][e], -1.0f);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) g[e] = fmaf(gA, Y[v][e], gB);
+        }
+        // annealed entropy term gamma_t (-2a) (2p - 1)^(a - 1) (Eq. 7)
+        if (c.half_pow == 1) {   // a = 4, the paper's exponent
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float u = fmaf(2.0f, o.P[v][e], -1.0f);
+                g[e] = fmaf(c.ent_coef, u * (u * u), g[e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float u = fmaf(2.0f, o.P[v][e], -1.0f);
+                const float u2 = u * u;
+                float upow = u;
+                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
+                g[e] = fmaf(c.ent_coef, upow, g[e]);
+            }
+        }
+        // cross-replica communication (Eq. 10)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) g[e] = fmaf(comm_coef, o.P[v][e] - mean, g[e]);
+        if (c.grad_dbg) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) c.grad_dbg[rbase + off + e] = g[e];
+        }
+        // Langevin noise, four replicas per Philox call
+        float xi[VEC];
+#pragma unroll
+        for (int e4 = 0; e4 < VEC; e4 += 4)
+            gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)((off + e4) >> 2), (uint32_t)c.t, xi + e4);
         float pn[VEC], M[VEC], V[VEC];
         VecT<T>::unpack(o.M[v], M);
         VecT<T>::unpack(o.V[v], V);
         bool bad = false;
-        // four replicas per Philox call; fully unrolled (register arrays need
-        // compile-time indices)
 #pragma unroll
-        for (int e4 = 0; e4 < VEC; e4 += 4)
-#pragma unroll
-        for (int e = e4; e < e4 + 4; ++e) {
-            float xi[4];
-            if (e == e4) gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)((off + e4) >> 2), (uint32_t)c.t, xi);
-            float csv = 0.0f;
-            if (c.kind == kMaxClique) csv = c.cs_cur[off + e];
-            const float p = o.P[v][e];
-            const float y = Y[v][e];
-            float g;
-            if (c.kind == kMIS) g = fmaf(c.lambda, y, -1.0f);
-            else if (c.kind == kMaxCut) g = fmaf(2.0f, y, -dsum);
-            else g = fmaf(c.lambda, (csv - 0.5f) - y, -1.0f);
-            const float u = fmaf(2.0f, p, -1.0f);
-            const float u2 = u * u;
-            float upow = u * u2;                       // a = 4, the paper's exponent
-            if (c.half_pow != 1) {
-                upow = u;
-                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
-            }
-            g = fmaf(c.ent_coef, upow, g);
-            if (c.alpha != 0.0f) g = fmaf(-c.alpha * inv_std, p - mean, g);
-            if (c.grad_dbg) c.grad_dbg[rbase + off + e] = g;
-            const float mn = fmaf(c.b1, M[e], (1.0f - c.b1) * g);
-            const float vn = fmaf(c.b2, V[e], (1.0f - c.b2) * (g * g));
+        for (int e = 0; e < VEC; ++e) {
+            // AdamW with decoupled decay (Sec. 3.4), noise sqrt(2 lr T) xi (Eq. 11), clamp
+            const float mn = fmaf(c.b1, M[e], om_b1 * g[e]);
+            const float vn = fmaf(c.b2, V[e], om_b2 * (g[e] * g[e]));
             const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
-            float q = p * c.decay;
-            q = fmaf(-c.step_size, __fdividef(mn, denom), q);
-            q = fmaf(c.noise_scale, xi[e - e4], q);
+            float q = o.P[v][e] * c.decay;
+            q = fmaf(-c.step_size, mn * rcp_ftz(denom), q);
+            q = fmaf(c.noise_scale, xi[e], q);
             bad |= !(fabsf(q) <= 3.0e38f);             // NaN or Inf anywhere upstream lands in q
             pn[e] = fminf(fmaxf(q, 0.0f), 1.0f);
             M[e] = mn;

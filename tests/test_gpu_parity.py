@@ -72,6 +72,34 @@ def test_init_state_is_the_oracle_draw(prec):
 
 
 # --------------------------------------------------------- single step ---
+@pytest.mark.parametrize("seed", [7, 0xFFFFFFFF00000001])
+def test_noise_field_matches_oracle(seed):
+    """Two steps from one state that differ only in the temperature differ by
+    sqrt(2 lr T) xi (Eq. 11): the kernel's Gaussians against the oracle's Box-Muller
+    draws, element by element. 192k draws include about a hundred uniforms within
+    2^-10 of 1, where the radius takes its series branch."""
+    n, S, t = 3000, 64, 4
+    g = G.erdos_renyi(n, 0.002, 3)
+    pT = Params(S=S, steps=10, lr=0.1, temperature=1e-3, alpha_comm=0.0, seed=seed, precision=FP32)
+    X0 = np.full((n, S), 0.5, np.float32)
+    zeros = np.zeros((n, S), np.float32)
+    out = []
+    for p in (pT, pT.with_(temperature=0.0)):
+        run = make_run(MIS, g, p)
+        run.set_state(0, X0, zeros, zeros, t)
+        run.steps(1)
+        out.append(run.get_state(0)[0].astype(np.float64))
+    assert out[0].min() > 0.0 and out[0].max() < 1.0          # no clamping: the difference is the noise
+    sigma = float(np.float32(np.sqrt(2.0 * float(np.float32(0.1)) * float(np.float32(1e-3)))))
+    xi_gpu = (out[0] - out[1]) / sigma
+    xi = oracle.noise_field(n, S, seed, t)
+    # the fused q + sigma xi rounds once (half an ulp of [1/4, 1) is at most 2^-25), plus the
+    # FP32 radius and the hardware sine/cosine (absolute error ~4e-7 times the radius)
+    tol = 1.05 * 2.0 ** -25 / sigma + 1e-6 * (1.0 + 2.0 * np.abs(xi))
+    assert_within("xi", xi_gpu, xi, tol)
+    assert abs(xi.mean()) < 0.02 and abs(xi.std() - 1.0) < 0.01
+
+
 @pytest.mark.parametrize("prec", [FP32, BF16])
 @pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
 @pytest.mark.parametrize("S", [8, 37, 128])

@@ -73,25 +73,33 @@ def read_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+# device symbol of each step kernel variant (as ncu lists it)
+KERNEL_SYMBOL = {"direct": "qqa_step_kernel", "staged": "qqa_step_tiled_kernel", "stream": "qqa_step_stream_kernel",
+                 "dense": "qqa_step_dense_kernel", "pipe": "qqa_step_pipe_kernel"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources the step kernel variant is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_02135_gb300", "csrc")
-    for name in ("step_impl.cuh", "qqa_internal.cuh"):
+    names = ["step_impl.cuh", "qqa_internal.cuh"] + (["step_dense.cu"] if kernel == "dense" else [])
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, kernel: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    only if it was taken on the current kernel source."""
+    only if it was taken on the same kernel variant and its current source."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != kernel_source_hash():
+    m_k = re.search(r"kernel_variant:\s*(\w+)", text)
+    if not m_sha or not m_b or not m_k or m_k.group(1) != kernel or m_sha.group(1) != kernel_source_hash(kernel):
         return None
     return float(m_b.group(1))
 
@@ -283,7 +291,7 @@ def run_ours(args):
     kinds = [inst.kind for inst in wl.instances]
     probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
     params = [qqa.make_params(inst.params) for inst in wl.instances]
-    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3, "dense": 4}[args.kernel],
+    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3, "dense": 4, "pipe": 5}[args.kernel],
                            kernel_param=args.kernel_param, group_lanes=args.group_lanes,
                            vec_per_lane=args.vec_per_lane, block_threads=args.block_threads)
     tuned_us = None
@@ -342,9 +350,10 @@ def run_ours(args):
     alg_bytes = algorithmic_bytes_per_launch(wl)
     peak, peak_kind = read_peak()
     achieved = alg_bytes / avg_launch_s / 1e9
+    variant = ["auto", "direct", "staged", "stream", "dense", "pipe"][run.config().kernel]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(args.workload), "peak_source": peak_kind,
-                "kernel": "qqa_step_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic": profiled_traffic(args.workload, variant), "peak_source": peak_kind,
+                "kernel": KERNEL_SYMBOL[variant], "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_us": avg_launch_s * 1e6, "step_share_of_device_time": step_ms / sum(ms)}
 
     # end to end through the public API with host buffers (CSR in, results out)
@@ -421,7 +430,7 @@ def run_ours(args):
                    "anneal_steps": K, "round_every": R, "precision": "fp32" if prec == W.FP32 else "bf16",
                    "l2": "flushed between timed anneals (512 MB write)",
                    "parallelism": f"instances x{world} ranks" if world > 1 else "single GPU",
-                   "launch": {"kernel": ["auto", "direct", "staged", "stream", "dense"][run.config().kernel],
+                   "launch": {"kernel": ["auto", "direct", "staged", "stream", "dense", "pipe"][run.config().kernel],
                               "group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
                               "kernel_param": run.config().kernel_param,
                               "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
@@ -518,7 +527,7 @@ def main():
     ap.add_argument("--workload", default="mis_er700_800",
                     choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512",
                              "serving"])
-    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense", "pipe"], default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
     ap.add_argument("--vec-per-lane", type=int, default=0)

@@ -49,7 +49,9 @@ extern "C" {
 typedef enum { QQA_MIS = 0, QQA_MAXCUT = 1, QQA_MAXCLIQUE = 2 } qqa_kind;
 typedef enum { QQA_FP32 = 0, QQA_BF16 = 1 } qqa_precision;
 
-/* Optional device allocator (e.g. a framework's caching allocator). */
+/* Optional device allocator (e.g. a framework's caching allocator). It must
+ * return memory aligned to at least 16 bytes (cudaMalloc and PyTorch's caching
+ * allocator give 256 / 512); qqa_run_add fails with QQA_EINVAL otherwise. */
 typedef struct qqa_allocator {
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
     void (*free)(void *ptr, void *stream, void *ctx);
@@ -102,6 +104,9 @@ typedef struct qqa_params {
  *                 in tensor memory - fused with the rest of the step; needs
  *                 an n_pad^2 fp16 adjacency per instance, n_pad = n rounded
  *                 up to 128; edge weights must be exact in fp16, |w| <= 2048)
+ *                 or QQA_KERNEL_PIPE (sparse graphs: every warp bulk-copies
+ *                 the next rows it owns of p, m and v into its own shared-
+ *                 memory double buffer while it updates the current ones)
  *   kernel_param: staged: row groups per warp (2, 4, 8);
  *                 stream: neighbour rows prefetched per row (4, 8);
  *                 dense: reported MMA width (64, 128, 256)
@@ -111,6 +116,7 @@ typedef struct qqa_params {
 #define QQA_KERNEL_STAGED 2
 #define QQA_KERNEL_STREAM 3
 #define QQA_KERNEL_DENSE 4
+#define QQA_KERNEL_PIPE 5
 typedef struct qqa_launch_config {
     int32_t group_lanes;
     int32_t vec_per_lane;
@@ -260,7 +266,8 @@ int qqa_round_eval(qqa_run *r, void *stream, int64_t *obj, int64_t *viol, uint8_
 int qqa_run_get_state(qqa_run *r, int32_t slot, void *stream, float *X, float *m, float *v, int32_t *t);
 /*
  * Overwrite one slot's state from host FP32 arrays [n][S] (values of X must
- * lie in [0,1]) and set its step count to t (0 <= t <= steps). BF16 runs
+ * lie in [0,1], m must be finite and v finite and >= 0; QQA_EINVAL otherwise)
+ * and set its step count to t (0 <= t <= steps). BF16 runs
  * keep X as the FP32 master and round it (and m, v) to BF16 storage.
  * Checkpoint/resume: set_state(get_state()) continues bit-identically.
  */

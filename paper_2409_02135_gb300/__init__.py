@@ -18,7 +18,7 @@ import ctypes
 import numpy as np
 
 from ._lib import (  # noqa: F401
-    BF16, FP32, KERNEL_AUTO, KERNEL_DENSE, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
+    BF16, FP32, KERNEL_AUTO, KERNEL_DENSE, KERNEL_DIRECT, KERNEL_PIPE, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
     QQAError, check, load, qqa_allocator, qqa_launch_config, qqa_params, qqa_request_info, ALLOC_FN, FREE_FN,
     SIGNATURES, REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED,
 )

@@ -23,7 +23,7 @@ ERROR_NAMES = {QQA_EINVAL: "EINVAL", QQA_ENOMEM: "ENOMEM", QQA_ECUDA: "ECUDA", Q
 
 MIS, MAXCUT, MAXCLIQUE = 0, 1, 2
 FP32, BF16 = 0, 1
-KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, KERNEL_DENSE = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, KERNEL_DENSE, KERNEL_PIPE = 0, 1, 2, 3, 4, 5
 
 
 class qqa_params(ctypes.Structure):

@@ -34,6 +34,9 @@ TiledFn step_tiled_kernel_bf16(int G, int VPL, int RPW);
 StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
 StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
 StepFn step_dense_kernel_fp32(int N);
+using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
+PipeFn step_pipe_kernel_fp32(int G, int VPL);
+PipeFn step_pipe_kernel_bf16(int G, int VPL);
 int dense_threads();
 int dense_smem_bytes(int N);
 }  // namespace qqa
@@ -251,6 +254,8 @@ struct qqa_run {
     bool dynamic = false;             // slots come and go: always launch the full persistent grid
     int32_t dense_N = 0;              // > 0: tensor-core step (MMA width = replicas covered)
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
+    PipeFn pipe_fn = nullptr;         // set when the pipelined kernel is used
+    int32_t pipe_buf = 0;             // bytes of one of its two shared-memory buffers
     int32_t chunk_rows = 0, buf_elems = 0;
     Alloc alloc;
     InstDesc *d_descs = nullptr;
@@ -304,7 +309,8 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     if (mode == QQA_KERNEL_AUTO)
         mode = (staged_hint && (c.block_threads == 0 || c.block_threads == 256)) ? QQA_KERNEL_STAGED : QQA_KERNEL_DIRECT;
     if (mode == QQA_KERNEL_AUTO) mode = QQA_KERNEL_DIRECT;
-    if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_DENSE) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
+    if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_PIPE) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
+    r->pipe_fn = nullptr;
     if (mode == QQA_KERNEL_DENSE) {
         if (r->prec != kFP32) return fail(QQA_EINVAL, "the dense tensor-core step needs an FP32 run");
         const int N = r->S_max_pad <= 64 ? 64 : (r->S_max_pad <= 128 ? 128 : (r->S_max_pad <= 256 ? 256 : 0));
@@ -357,6 +363,41 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->tiled_fn, block, r->smem));
         r->rows_per_tile = (block / 32) * rpw * (32 / G);
         r->step_fn = nullptr;
+    } else if (mode == QQA_KERNEL_PIPE) {
+        r->tiled_fn = nullptr;
+        r->step_fn = nullptr;
+        rpw = 0;
+        r->pipe_fn = r->prec == kFP32 ? step_pipe_kernel_fp32(G, VPL) : step_pipe_kernel_bf16(G, VPL);
+        if (!r->pipe_fn) return fail(QQA_EINVAL, "no pipelined kernel for G=%d VPL=%d", G, VPL);
+        if (block < 32 || block > 256 || block % 32)
+            return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
+        // every warp owns two buffers, each holding one tile's rows of p (FP32),
+        // m and v; a tile is the warp's 32 / G rows (one per lane group)
+        auto smem_for = [&](int b, int32_t &buf) {
+            buf = (32 / G) * r->S_max_pad * (4 + 2 * tb);
+            return 128 + (b / 32) * 2 * buf;
+        };
+        int max_smem = 0;
+        QQA_CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (c.block_threads == 0) {
+            int best_warps = -1;
+            for (int b : {256, 128, 64}) {
+                int32_t buf = 0;
+                const int sm = smem_for(b, buf);
+                if (sm > max_smem) continue;
+                int o = 0;
+                QQA_CK(cudaFuncSetAttribute(r->pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, r->pipe_fn, b, sm));
+                if (o * b / 32 > best_warps) { best_warps = o * b / 32; block = b; }
+            }
+        }
+        r->smem = smem_for(block, r->pipe_buf);
+        if (r->smem > max_smem)
+            return fail(QQA_EINVAL, "pipelined kernel needs %d bytes of shared memory (S=%d, %d threads)", r->smem,
+                        r->S_max_pad, block);
+        QQA_CK(cudaFuncSetAttribute(r->pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->pipe_fn, block, r->smem));
+        r->rows_per_tile = 32 / G;
     } else if (mode == QQA_KERNEL_STREAM) {
         r->tiled_fn = nullptr;
         r->step_fn = r->prec == kFP32 ? step_stream_kernel_fp32(G, VPL, rpw) : step_stream_kernel_bf16(G, VPL, rpw);
@@ -639,6 +680,12 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
         free_slot(r, k, st);
         return fail(QQA_ENOMEM, "device allocation for instance state failed (n=%d, S=%d)", s.n, s.S);
     }
+    const void *state_ptrs[5] = {d.X[0], d.X[1], d.master, d.m, d.v};
+    for (const void *q : state_ptrs)
+        if (q && ((uintptr_t)q & 15u)) {
+            free_slot(r, k, st);
+            return fail(QQA_EINVAL, "the allocator returned state memory that is not 16-byte aligned");
+        }
     if (r->dense_N) {
         if (prob->max_abs_w > 2048) {
             free_slot(r, k, st);
@@ -840,6 +887,9 @@ static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream
         if (r->tiled_fn)
             r->tiled_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                      r->d_status, i, r->chunk_rows, r->buf_elems);
+        else if (r->pipe_fn)
+            r->pipe_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
+                                                                    r->d_status, i, r->pipe_buf);
         else
             r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                     r->d_status, i);
@@ -1073,8 +1123,11 @@ extern "C" int qqa_run_set_state(qqa_run *r, int32_t k, void *stream, const floa
     SlotHost &s = r->slots[k];
     if (t < 0 || t > s.K) return fail(QQA_EINVAL, "t = %d outside [0, %d]", t, s.K);
     const size_t elems = (size_t)s.n * s.S;
-    for (size_t e = 0; e < elems; ++e)
+    for (size_t e = 0; e < elems; ++e) {
         if (!(X[e] >= 0.0f && X[e] <= 1.0f)) return fail(QQA_EINVAL, "X[%zu] = %g outside [0, 1]", e, (double)X[e]);
+        if (!(std::fabs(m[e]) <= 3.0e38f)) return fail(QQA_EINVAL, "m[%zu] = %g is not finite", e, (double)m[e]);
+        if (!(v[e] >= 0.0f && v[e] <= 3.0e38f)) return fail(QQA_EINVAL, "v[%zu] = %g outside [0, inf)", e, (double)v[e]);
+    }
     cudaStream_t st = (cudaStream_t)stream;
     int rc = ensure_scratch(r, elems * 12, st);
     if (rc) return rc;

@@ -150,24 +150,63 @@ __device__ __forceinline__ float neg2_log_unit(uint32_t r)
     return delta < 9.765625e-4f ? series : via_log2;
 }
 
-// Four standard normals for replicas 4q..4q+3 of node i at step t (stream tag 1):
-// Box-Muller on the uniform pairs (r0, r1) and (r2, r3): radius sqrt(-2 ln u1),
-// angle 2 pi u2. The angle is taken as 2 pi (u2 - 1/2) - exact in FP32 - so the
-// hardware sine/cosine see (-pi, pi], and the sign flip restores cos/sin(2 pi u2).
+// NQ independent Philox4x32-10 streams in lockstep: one key schedule for all
+// of them, and NQ-fold instruction-level parallelism.
+template <int NQ>
+__device__ __forceinline__ void philox10_multi(U4 (&c)[NQ], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            const uint64_t p0 = (uint64_t)0xD2511F53u * c[j].x;
+            const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[j].z;
+            c[j] = U4{(uint32_t)(p1 >> 32) ^ c[j].y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c[j].w ^ k1, (uint32_t)p0};
+        }
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Box-Muller pair from the uniform words (ra, rb): radius sqrt(-2 ln u1) with
+// u1 from ra, angle 2 pi u2 with u2 from rb. The angle is taken as
+// 2 pi (u2 - 1/2) = ((rb >> 8) - (2^23 - 1)) * (2 pi 2^-24) - exact in FP32 up to
+// the one rounding of the product, so the hardware sine/cosine see (-pi, pi];
+// the sign flip restores cos/sin(2 pi u2).
+__device__ __forceinline__ void box_muller(uint32_t ra, uint32_t rb, float &z0, float &z1)
+{
+    const float rad = sqrt_nonneg(neg2_log_unit(ra));
+    const float ang = (float)((int32_t)(rb >> 8) - 8388607) * 0x1.921FB6p-22f;   // fl(2 pi) * 2^-24
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    z0 = -rad * cs;
+    z1 = -rad * sn;
+}
+
+// Standard normals for the NQ replica quads q[j] of node i at step t (stream
+// tag 1): out[4j..4j+3] are replicas 4 q[j] .. 4 q[j] + 3, Box-Muller on the
+// uniform pairs (r0, r1) and (r2, r3) of each quad's Philox block.
+template <int NQ>
+__device__ __forceinline__ void gauss_quads(uint32_t seed_lo, uint32_t seed_hi, uint32_t i, const uint32_t (&q)[NQ],
+                                            uint32_t t, float *out)
+{
+    U4 c[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) c[j] = U4{i, q[j], t, 1u};
+    philox10_multi<NQ>(c, seed_lo, seed_hi);
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        box_muller(c[j].x, c[j].y, out[4 * j], out[4 * j + 1]);
+        box_muller(c[j].z, c[j].w, out[4 * j + 2], out[4 * j + 3]);
+    }
+}
+
+// Four standard normals for replicas 4q..4q+3 of node i at step t.
 __device__ __forceinline__ void gauss4(uint32_t seed_lo, uint32_t seed_hi, uint32_t i, uint32_t q, uint32_t t,
                                        float out[4])
 {
-    const U4 r = philox10(U4{i, q, t, 1u}, seed_lo, seed_hi);
-    const float two_pi = 6.28318530717958647692f;
-    float s0, c0, s1, c1;
-    const float rad0 = sqrt_nonneg(neg2_log_unit(r.x));
-    __sincosf(two_pi * (bits_to_unit(r.y) - 0.5f), &s0, &c0);
-    const float rad1 = sqrt_nonneg(neg2_log_unit(r.z));
-    __sincosf(two_pi * (bits_to_unit(r.w) - 0.5f), &s1, &c1);
-    out[0] = -rad0 * c0;
-    out[1] = -rad0 * s0;
-    out[2] = -rad1 * c1;
-    out[3] = -rad1 * s1;
+    const uint32_t qs[1] = {q};
+    gauss_quads<1>(seed_lo, seed_hi, i, qs, t, out);
 }
 
 // Four uniforms for the initial state (stream tag 0, step 0).

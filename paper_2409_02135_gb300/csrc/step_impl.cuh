@@ -145,15 +145,18 @@ __device__ __forceinline__ void accumulate_row(float (&Y)[VPL][VecT<T>::N], cons
 }
 
 // Direct gather of the whole neighbour list of `row` from global memory.
-// Unweighted graphs (MIS, clique, unit max-cut) take a lean path: plain adds
-// (exactly fmaf(1, x, y)) and the weighted degree is the row length.
+// Neighbours go in batches of UNR whose loads are all in flight together (a
+// short row costs one round trip to L2); slots past the end of the row load
+// nothing and add zero, which leaves Y unchanged. Unweighted graphs (MIS,
+// clique, unit max-cut) take a lean path: plain adds (exactly fmaf(1, x, y))
+// and the weighted degree is the row length.
 template <typename T, int G, int VPL>
 __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, const T *__restrict__ Xc, int row,
                                               int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
                                               float &dsum)
 {
     constexpr int VEC = VecT<T>::N;
-    constexpr int UNR = VPL >= 4 ? 1 : (VPL == 2 ? 2 : 4);   // neighbours in flight per batch
+    constexpr int UNR = VPL >= 4 ? 2 : (VPL == 2 ? 4 : 8);   // neighbours in flight per batch
     const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
     const int32_t *__restrict__ colp = d->col;
     const int32_t *__restrict__ wp = d->w;
@@ -170,48 +173,38 @@ __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, co
     for (int kb = k0; kb < k1; kb += G) {
         const int myk = kb + gl;
         int jl = 0;
-        float wl = 1.0f;
+        float wl = 0.0f;
         if (myk < k1) {
             jl = __ldg(colp + myk);
-            if (wp) wl = (float)__ldg(wp + myk);
+            wl = wp ? (float)__ldg(wp + myk) : 1.0f;
         }
+        if (wp) dsum += group_sum<G>(wl, gmask);
         const int cnt = min(G, k1 - kb);
-        int q = 0;
-        for (; q + UNR <= cnt; q += UNR) {
+        for (int q = 0; q < cnt; q += UNR) {
             uint4 raw[UNR][VPL];   // packed until accumulated: 4 registers per 16-byte slice
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
                 const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q + u, G) * S_pad;
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) raw[u][v] = __ldg(reinterpret_cast<const uint4 *>(rowp + offs[v]));
+                for (int v = 0; v < VPL; ++v) {
+                    raw[u][v] = make_uint4(0u, 0u, 0u, 0u);
+                    if (q + u < cnt) raw[u][v] = __ldg(reinterpret_cast<const uint4 *>(rowp + offs[v]));
+                }
             }
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const float w = wp ? __shfl_sync(gmask, wl, q + u, G) : 1.0f;
-                if (wp) dsum += w;
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) {
                     if (wp == nullptr) {
                         VecT<T>::add_to(raw[u][v], Y[v]);
                     } else {
+                        const float w = __shfl_sync(gmask, wl, q + u, G);
                         float x[VEC];
                         VecT<T>::unpack(raw[u][v], x);
 #pragma unroll
                         for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
                     }
                 }
-            }
-        }
-        for (; q < cnt; ++q) {
-            const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q, G) * S_pad;
-            const float w = wp ? __shfl_sync(gmask, wl, q, G) : 1.0f;
-            if (wp) dsum += w;
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                float x[VEC];
-                VecT<T>::load_ro(rowp + offs[v], x);
-#pragma unroll
-                for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
             }
         }
     }
@@ -313,6 +306,19 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     const float gB = c.kind == kMaxCut ? -dsum : -1.0f;
     const float om_b1 = 1.0f - c.b1, om_b2 = 1.0f - c.b2;
 
+    // Langevin noise: all of the lane's replica quads in one lockstep Philox
+    // pass when they fit in 16 registers, else one pass per vector
+    constexpr bool kRowNoise = VPL * VEC <= 16;
+    float xi_row[kRowNoise ? VPL : 1][VEC];
+    if (kRowNoise) {
+        uint32_t qs[VPL * VEC / 4];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int e4 = 0; e4 < VEC; e4 += 4) qs[(v * VEC + e4) / 4] = (uint32_t)(((v * G + gl) * VEC + e4) >> 2);
+        gauss_quads<VPL * VEC / 4>(d->seed_lo, d->seed_hi, (uint32_t)row, qs, (uint32_t)c.t, &xi_row[0][0]);
+    }
+
     // The per-instance choices (problem kind, entropy exponent, gradient dump)
     // branch once per 16-byte vector, so the element loops are straight-line.
 #pragma unroll
@@ -351,30 +357,35 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
 #pragma unroll
             for (int e = 0; e < VEC; ++e) c.grad_dbg[rbase + off + e] = g[e];
         }
-        // Langevin noise, four replicas per Philox call
-        float xi[VEC];
+        float xi_vec[kRowNoise ? 1 : VEC];
+        if (!kRowNoise) {
+            uint32_t qs[VEC / 4];
 #pragma unroll
-        for (int e4 = 0; e4 < VEC; e4 += 4)
-            gauss4(d->seed_lo, d->seed_hi, (uint32_t)row, (uint32_t)((off + e4) >> 2), (uint32_t)c.t, xi + e4);
+            for (int e4 = 0; e4 < VEC; e4 += 4) qs[e4 / 4] = (uint32_t)((off + e4) >> 2);
+            gauss_quads<VEC / 4>(d->seed_lo, d->seed_hi, (uint32_t)row, qs, (uint32_t)c.t, xi_vec);
+        }
+        const float *xi = kRowNoise ? xi_row[kRowNoise ? v : 0] : xi_vec;
         float pn[VEC], M[VEC], V[VEC];
         VecT<T>::unpack(o.M[v], M);
         VecT<T>::unpack(o.V[v], V);
-        bool bad = false;
+        float vsum = 0.0f;
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
-            // AdamW with decoupled decay (Sec. 3.4), noise sqrt(2 lr T) xi (Eq. 11), clamp
+            // AdamW with decoupled decay (Sec. 3.4), noise sqrt(2 lr T) xi (Eq. 11),
+            // clamp to [0, 1] (saturation; it maps NaN to 0)
             const float mn = fmaf(c.b1, M[e], om_b1 * g[e]);
             const float vn = fmaf(c.b2, V[e], om_b2 * (g[e] * g[e]));
             const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
             float q = o.P[v][e] * c.decay;
             q = fmaf(-c.step_size, mn * rcp_ftz(denom), q);
-            q = fmaf(c.noise_scale, xi[e], q);
-            bad |= !(fabsf(q) <= 3.0e38f);             // NaN or Inf anywhere upstream lands in q
-            pn[e] = fminf(fmaxf(q, 0.0f), 1.0f);
+            pn[e] = __saturatef(fmaf(c.noise_scale, xi[e], q));
+            vsum += vn;
             M[e] = mn;
             V[e] = vn;
         }
-        if (bad) atomicAdd(&status->nonfinite, 1ULL);
+        // p, m and v enter finite (the state is checked on the way in), so any
+        // NaN, Inf or overflow of the gradient shows in the second moment
+        if (!(vsum <= 3.0e38f)) atomicAdd(&status->nonfinite, 1ULL);
         VecT<T>::store(Xn + rbase + off, pn);
         if (d->master) {
             for (int k = 0; k < VEC; k += 4)
@@ -689,6 +700,147 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
         }
         if (clique) clique_tile_end(c, sh_colsum);
         else __syncthreads();   // hdr->lo / hi and sidx are rewritten by the next tile
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-pipelined kernel for sparse graphs. A tile is the 32 / G consecutive
+// rows of one warp (one row per lane group), so its own data (p^t - the FP32
+// master in BF16 runs -, m and v) are three contiguous slabs. Every warp walks
+// its own tiles and owns a double buffer in shared memory: while it gathers
+// and updates one tile, lane 0 has the next tile's three slabs in flight to the
+// other buffer (bulk copies, completion counted on that buffer's mbarrier).
+// The HBM latency of the streamed state is hidden without registers, and with
+// no block-wide barriers the warps of an SM drift apart, so one warp's gather
+// latency is covered by the others' epilogues.
+// ---------------------------------------------------------------------------
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void load_own_smem(const unsigned char *buf, int R, int S_pad, int lrow, int gl,
+                                              OwnRow<T, G, VPL> &o)
+{
+    constexpr int VEC = VecT<T>::N;
+    const float *sP = reinterpret_cast<const float *>(buf) + (size_t)lrow * S_pad;
+    const T *sM = reinterpret_cast<const T *>(buf + (size_t)R * S_pad * sizeof(float)) + (size_t)lrow * S_pad;
+    const T *sV = sM + (size_t)R * S_pad;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int off = (v * G + gl) * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) o.P[v][e] = 0.0f;
+        o.M[v] = make_uint4(0, 0, 0, 0);
+        o.V[v] = make_uint4(0, 0, 0, 0);
+        if (off < S_pad) {
+#pragma unroll
+            for (int k = 0; k < VEC; k += 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(sP + off + k);
+                o.P[v][k] = a.x; o.P[v][k + 1] = a.y; o.P[v][k + 2] = a.z; o.P[v][k + 3] = a.w;
+            }
+            o.M[v] = *reinterpret_cast<const uint4 *>(sM + off);
+            o.V[v] = *reinterpret_cast<const uint4 *>(sV + off);
+        }
+    }
+}
+
+template <typename T, int G, int VPL>
+__global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__restrict__ descs,
+                                                            const Tile *__restrict__ tiles,
+                                                            const int32_t *__restrict__ num_tiles_p,
+                                                            RunStatus *__restrict__ status, int32_t r,
+                                                            int32_t buf_bytes)
+{
+    constexpr int R = 32 / G;   // rows of a tile: one per lane group of the warp
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gl = lane & (G - 1);
+    const int grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int nwarps = blockDim.x >> 5;
+    // header: two barriers per warp (at most 8 warps); then each warp's two buffers
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
+    unsigned char *const buf0 = smem_raw + 128 + (size_t)warp * 2 * buf_bytes;   // buffer b at buf0 + b * buf_bytes
+    const int num_tiles = *num_tiles_p;
+    const int W = gridDim.x * nwarps;
+    const int first = blockIdx.x * nwarps + warp;
+
+    if (lane == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+
+    // Lane 0 only: start the copies of `tile`'s slabs into buffer b (nothing for
+    // a finished instance, whose tile the warp skips). Returns whether it did.
+    auto issue = [&](int tile, int b) -> bool {
+        const Tile tl = tiles[tile];
+        const InstDesc *__restrict__ d = descs + tl.slot;
+        const int t = d->t + r;
+        if (t >= d->K) return false;
+        const int rows = min(R, d->n - tl.row0);
+        const size_t e0 = (size_t)tl.row0 * d->S_pad;
+        const uint32_t pbytes = (uint32_t)(rows * d->S_pad * sizeof(float));
+        const uint32_t sbytes = (uint32_t)(rows * d->S_pad * sizeof(T));
+        const float *psrc = d->master ? d->master + e0 : reinterpret_cast<const float *>(d->X[t & 1]) + e0;
+        unsigned char *dst = buf0 + (size_t)b * buf_bytes;
+        const size_t mofs = (size_t)R * d->S_pad * sizeof(float);
+        const size_t vofs = mofs + (size_t)R * d->S_pad * sizeof(T);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&mbar[b], pbytes + 2 * sbytes);
+        tma_bulk_load(dst, psrc, pbytes, &mbar[b]);
+        tma_bulk_load(dst + mofs, reinterpret_cast<const T *>(d->m) + e0, sbytes, &mbar[b]);
+        tma_bulk_load(dst + vofs, reinterpret_cast<const T *>(d->v) + e0, sbytes, &mbar[b]);
+        return true;
+    };
+
+    // completed phases of each buffer's barrier (warp-uniform), and lane 0's
+    // record of a copy in flight into the buffer not being read
+    uint32_t uses0 = 0u, uses1 = 0u;
+    bool next_pending = false;
+    int b = 0;
+    if (lane == 0 && first < num_tiles) issue(first, 0);
+    for (int tile = first; tile < num_tiles; tile += W, b ^= 1) {
+        // buffer b^1 was last read in the previous iteration, which ended in __syncwarp
+        if (lane == 0) next_pending = tile + W < num_tiles && issue(tile + W, b ^ 1);
+        const Tile tl = tiles[tile];
+        const InstDesc *__restrict__ d = descs + tl.slot;
+        const int t = d->t + r;
+        if (t >= d->K) continue;   // finished instance: no copy was issued, nothing is read
+        const StepCtx c = make_ctx(d, t, r);
+        const bool clique = (c.kind == kMaxClique);
+        if (clique && tl.row0 == 0) {   // zero the column sums step t+1 accumulates into
+            float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
+            for (int s = lane; s < c.S_pad; s += 32) cs_zero[s] = 0.0f;
+        }
+        const int row = tl.row0 + grp;
+        float Y[VPL][VecT<T>::N];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int e = 0; e < VecT<T>::N; ++e) Y[v][e] = 0.0f;
+        float dsum = 0.0f;
+        if (row < c.n)
+            gather_direct<T, G, VPL>(d, reinterpret_cast<const T *>(d->X[t & 1]), row, c.S_pad, gl, gmask, Y, dsum);
+        const uint32_t parity = (b ? uses1 : uses0) & 1u;
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[b], parity));
+        if (!ok) {
+            // the slabs did not arrive in time: flag it, let every copy still in
+            // flight land (bounded), and leave without touching the state
+            if (lane == 0) {
+                atomicAdd(&status->timeouts, 1ULL);
+                if (next_pending) mbar_wait_bounded(&mbar[b ^ 1], (b ? uses0 : uses1) & 1u);
+                mbar_wait_bounded(&mbar[b], parity);
+            }
+            __syncwarp();
+            return;
+        }
+        if (b) ++uses1; else ++uses0;
+        if (row < c.n) {
+            OwnRow<T, G, VPL> own;
+            load_own_smem<T, G, VPL>(buf0 + (size_t)b * buf_bytes, R, c.S_pad, grp, gl, own);
+            update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status, c.cs_next);
+        }
+        __syncwarp();   // every lane is done with buffer b
     }
 }
 

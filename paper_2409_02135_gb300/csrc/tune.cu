@@ -2,7 +2,8 @@
 //
 // The shape choices are the kernel variant (direct gather, cp.async stream
 // with 4 or 8 prefetched neighbours, TMA-staged with 2 or 4 row groups per
-// warp, and for FP32 runs of graphs up to 8192 nodes the tensor-core step),
+// warp, pipelined with the next tile's own rows bulk-copied ahead, and for
+// FP32 runs of graphs up to 8192 nodes the tensor-core step),
 // the lanes per node row G and 16-byte vectors per lane VPL that cover
 // S_max replicas, and the block size. Each candidate runs on a temporary run
 // of the caller's instances: one warm-up chunk, then `trial_steps` steps timed
@@ -79,6 +80,7 @@ extern "C" int qqa_autotune(qqa_problem *const *problems, const qqa_params *para
             for (int bt : {0, 128, 256}) cands.push_back(qqa_launch_config{G, VPL, bt, 0, 1, QQA_KERNEL_DIRECT, 0, 0});
             for (int nb : {4, 8}) cands.push_back(qqa_launch_config{G, VPL, 256, 0, 1, QQA_KERNEL_STREAM, nb, 0});
             for (int rpw : {2, 4}) cands.push_back(qqa_launch_config{G, VPL, 256, 0, 1, QQA_KERNEL_STAGED, rpw, 0});
+            for (int bt : {0, 128}) cands.push_back(qqa_launch_config{G, VPL, bt, 0, 1, QQA_KERNEL_PIPE, 0, 0});
         }
 
     cudaStream_t st = (cudaStream_t)stream;

@@ -213,6 +213,61 @@ def test_stream_kernel_equals_direct_kernel(kind, prec, S, layout):
         np.testing.assert_array_equal(va, vb)
 
 
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("prec,S,layout", [(BF16, 256, (16, 2, 128)), (BF16, 256, (32, 1, 256)), (FP32, 128, (32, 1, 64)),
+                                           (FP32, 200, (32, 2, 256)), (FP32, 30, (8, 1, 128)), (BF16, 40, (8, 1, 256)),
+                                           (FP32, 8, (2, 1, 64)), (BF16, 8, (1, 1, 32))])
+def test_pipe_kernel_equals_direct_kernel(kind, prec, S, layout):
+    """The pipelined kernel (own rows bulk-copied to shared memory one tile
+    ahead) runs the direct kernel's gather and epilogue, so states are bit for
+    bit the same; 413 nodes leave a ragged last tile for every tile height."""
+    G_, V_, B_ = layout
+    g = G.barabasi_albert(413, 3, 80 + kind)
+    if kind == MAXCUT:
+        rng = np.random.default_rng(kind)
+        u, v, _ = g.upper_edges()
+        g = G.from_edges(g.n, u, v, rng.integers(-2, 5, size=u.size))
+    p = Params(S=S, steps=100, alpha_comm=0.3, seed=13, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    a = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, B_, kernel=qqa.KERNEL_PIPE))
+    b = make_run(kind, g, p, config=qqa.LaunchConfig(G_, V_, B_, kernel=qqa.KERNEL_DIRECT))
+    assert a.config().kernel == qqa.KERNEL_PIPE and a.config().block_threads == B_
+    a.steps(60)
+    b.steps(60)
+    Xa, ma, va, _ = a.get_state(0)
+    Xb, mb, vb, _ = b.get_state(0)
+    if kind == MAXCLIQUE:   # column sums are float atomics: order-dependent rounding
+        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
+    else:
+        np.testing.assert_array_equal(Xa, Xb)
+        np.testing.assert_array_equal(ma, mb)
+        np.testing.assert_array_equal(va, vb)
+
+
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_pipe_kernel_single_step_parity_and_finished_instances(prec):
+    """Single steps of the pipelined kernel against the oracle, in a batch where
+    instances finish at different steps (their tiles are skipped: no copy is
+    started for them) while the others go on, automatic block size."""
+    gs = [G.random_regular(600, 3, 5), G.erdos_renyi(257, 0.03, 6), G.barabasi_albert(333, 4, 7)]
+    ps = [Params(S=64, steps=k, alpha_comm=0.2, seed=20 + k, precision=prec, gamma_min=-5.0)
+          for k in (12, 40, 25)]
+    run = make_run(MAXCUT, gs, ps, config=qqa.LaunchConfig(16, 1, 0, kernel=qqa.KERNEL_PIPE))
+    assert run.config().kernel == qqa.KERNEL_PIPE
+    for slot in range(3):                           # each check advances every instance one step
+        _check_step(MAXCUT, gs[slot], ps[slot], prec, run, slot=slot)
+    run.steps(30)                                   # instance 0 stops at 12, instance 2 at 25
+    t = [run.get_state(k)[3] for k in range(3)]
+    assert t == [12, 33, 25]
+    _check_step(MAXCUT, gs[1], ps[1], prec, run, slot=1)
+    ref = make_run(MAXCUT, gs, ps, config=qqa.LaunchConfig(16, 1, 0, kernel=qqa.KERNEL_DIRECT))
+    for k in range(3):
+        ref.step_debug(k)
+    ref.steps(30)
+    ref.step_debug(1)
+    for k in range(3):
+        np.testing.assert_array_equal(run.get_state(k)[0], ref.get_state(k)[0])
+
+
 def test_stream_kernel_single_step_parity_sparse_graph():
     g = G.random_regular(2000, 3, 4)
     p = Params(S=256, steps=500, alpha_comm=0.3, seed=0, precision=BF16, gamma_min=-5.0)
@@ -282,6 +337,31 @@ def test_staged_kernel_single_step_parity_dense_graph():
     assert run.config().kernel == qqa.KERNEL_STAGED
     run.steps(50)
     _check_step(MIS, g, p, FP32, run)
+
+
+@pytest.mark.parametrize("prec,kernel", [(FP32, qqa.KERNEL_DIRECT), (BF16, qqa.KERNEL_PIPE)])
+def test_non_finite_gradient_is_reported(prec, kernel):
+    """A gradient that overflows (lambda = 1e30 makes g^2 infinite) is counted in
+    the device status word and reported as QQA_ENONFINITE; the state stays in
+    [0, 1]. Non-finite moments are refused on the way in."""
+    g = _graph(MIS, 120, 0.1, 3)
+    p = Params(S=16, steps=20, lam=1e30, seed=4, precision=prec)
+    run = make_run(MIS, g, p, config=qqa.LaunchConfig(8, 1, 128, kernel=kernel))
+    run.steps(2)
+    with pytest.raises(qqa.QQAError) as err:
+        run.sync()
+    assert err.value.code == qqa.QQA_ENONFINITE
+    X = run.get_state(0)[0]
+    assert np.all((X >= 0) & (X <= 1))
+    ok = make_run(MIS, g, p.with_(lam=2.0))
+    X0, m0, v0, t0 = ok.get_state(0)
+    for bad_m, bad_v in ((np.inf, 0.0), (np.nan, 0.0), (0.0, -1.0), (0.0, np.inf)):
+        m1, v1 = m0.copy(), v0.copy()
+        m1[3, 5] = bad_m
+        v1[7, 1] = bad_v
+        with pytest.raises(qqa.QQAError) as err:
+            ok.set_state(0, X0, m1, v1, t0)
+        assert err.value.code == qqa.QQA_EINVAL
 
 
 # ---------------------------------------------------------- multi-step ---

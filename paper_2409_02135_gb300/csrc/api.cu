@@ -262,7 +262,8 @@ struct qqa_run {
     std::vector<InstDesc> h_descs;
     Tile *d_tiles = nullptr;
     int32_t tile_cap = 0;
-    int32_t *d_num_tiles = nullptr;
+    int32_t *d_num_tiles = nullptr;  // [0] tiles, [1] streaming cache hints on (state larger than L2)
+    int32_t tile_words[2] = {0, 0};
     int32_t num_tiles = 0;
     RunStatus *d_status = nullptr;
     float *d_scratch = nullptr;   // state import/export staging
@@ -479,7 +480,18 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
         drop_graphs(r);  // captured graphs hold the old tile pointer
     }
     if (nt) QQA_CK(cudaMemcpyAsync(r->d_tiles, tiles.data(), sizeof(Tile) * (size_t)nt, cudaMemcpyHostToDevice, st));
-    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, &nt, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // second word: the run's replica state (p^t, p^{t+1}, master, m, v) is larger
+    // than most of L2, so streaming kernels mark it evict-first
+    double state_bytes = 0.0;
+    const double per_elem = r->prec == kFP32 ? 16.0 : 12.0;
+    for (int32_t k = 0; k < r->capacity; ++k)
+        if (r->slots[k].active) state_bytes += per_elem * (double)r->slots[k].n * (double)r->slots[k].S_pad;
+    int dev = 0, l2 = 0;
+    QQA_CK(cudaGetDevice(&dev));
+    QQA_CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    r->tile_words[0] = nt;
+    r->tile_words[1] = state_bytes > 0.75 * (double)l2 ? 1 : 0;
+    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
     r->num_tiles = nt;
     return QQA_OK;
@@ -518,7 +530,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     r->h_descs.assign(capacity, InstDesc{});
     r->slots.resize(capacity);
     r->d_descs = (InstDesc *)r->alloc.get(sizeof(InstDesc) * (size_t)capacity, st);
-    r->d_num_tiles = (int32_t *)r->alloc.get(sizeof(int32_t), st);
+    r->d_num_tiles = (int32_t *)r->alloc.get(2 * sizeof(int32_t), st);
     r->d_status = (RunStatus *)r->alloc.get(sizeof(RunStatus), st);
     if (!r->d_descs || !r->d_num_tiles || !r->d_status) {
         qqa_run_destroy(r);
@@ -526,7 +538,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     }
     cudaError_t e = cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)capacity,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, 2 * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_status, 0, sizeof(RunStatus), st);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

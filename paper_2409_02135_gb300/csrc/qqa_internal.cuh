@@ -220,6 +220,41 @@ __device__ __forceinline__ void unif4(uint32_t seed_lo, uint32_t seed_hi, uint32
 }
 
 // ---------------------------------------------------------------------------
+// L2 cache policies (createpolicy) and the hinted 16-byte accesses that use
+// them: state streamed once per step is marked evict-first, the state vector
+// the next step gathers from is marked evict-last.
+// ---------------------------------------------------------------------------
+struct L2Policies {
+    uint64_t stream;   // read or written once per step
+    uint64_t keep;     // gathered again (p^t, p^{t+1})
+};
+
+__device__ __forceinline__ L2Policies make_l2_policies(bool hints)
+{
+    uint64_t first, last, normal;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(first));
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(last));
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(normal));
+    return hints ? L2Policies{first, last} : L2Policies{normal, normal};
+}
+
+__device__ __forceinline__ uint4 ld_nc_hint(const void *p, uint64_t pol)
+{
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_hint(void *p, uint4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // 16-byte vectors of replicas: 4 FP32 or 8 BF16 values.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -241,6 +276,11 @@ struct VecT<float> {
     __device__ __forceinline__ static void store(float *p, const float in[4])
     {
         *reinterpret_cast<float4 *>(p) = make_float4(in[0], in[1], in[2], in[3]);
+    }
+    __device__ __forceinline__ static uint4 pack(const float in[4])
+    {
+        return make_uint4(__float_as_uint(in[0]), __float_as_uint(in[1]), __float_as_uint(in[2]),
+                          __float_as_uint(in[3]));
     }
     __device__ __forceinline__ static void unpack(const uint4 a, float out[4])
     {

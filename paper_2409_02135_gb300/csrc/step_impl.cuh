@@ -144,22 +144,76 @@ __device__ __forceinline__ void accumulate_row(float (&Y)[VPL][VecT<T>::N], cons
     }
 }
 
-// Direct gather of the whole neighbour list of `row` from global memory.
-// Neighbours go in batches of UNR whose loads are all in flight together (a
-// short row costs one round trip to L2); slots past the end of the row load
-// nothing and add zero, which leaves Y unchanged. Unweighted graphs (MIS,
-// clique, unit max-cut) take a lean path: plain adds (exactly fmaf(1, x, y))
-// and the weighted degree is the row length.
-template <typename T, int G, int VPL>
-__device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, const T *__restrict__ Xc, int row,
-                                              int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
-                                              float &dsum)
+// Where a row's neighbours are: its CSR range and, for the lane group's first
+// batch, lane gl's neighbour index and weight (0 past the end of the row).
+struct RowIdx {
+    int k0, k1, jl;
+    float wl;
+};
+
+__device__ __forceinline__ RowIdx load_row_idx(const InstDesc *__restrict__ d, int row, int gl)
+{
+    RowIdx x{0, 0, 0, 0.0f};
+    if (row < d->n) {
+        x.k0 = __ldg(d->row_ptr + row);
+        x.k1 = __ldg(d->row_ptr + row + 1);
+        if (x.k0 + gl < x.k1) {
+            x.jl = __ldg(d->col + x.k0 + gl);
+            x.wl = d->w ? (float)__ldg(d->w + x.k0 + gl) : 1.0f;
+        }
+    }
+    return x;
+}
+
+// N neighbours q0..q0+N-1 of the lane group's current index batch: all loads
+// in flight together, then added in CSR order. Unweighted graphs add plainly
+// (exactly fmaf(1, x, y)).
+template <typename T, int G, int VPL, int N, bool HINT>
+__device__ __forceinline__ void gather_batch(const T *__restrict__ Xc, int jl, float wl, int q0, bool weighted,
+                                             const int (&offs)[VPL], int S_pad, unsigned gmask,
+                                             float (&Y)[VPL][VecT<T>::N], uint64_t pol_keep)
 {
     constexpr int VEC = VecT<T>::N;
-    constexpr int UNR = VPL >= 4 ? 2 : (VPL == 2 ? 4 : 8);   // neighbours in flight per batch
-    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
+    uint4 raw[N][VPL];   // packed until accumulated: 4 registers per 16-byte slice
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q0 + u, G) * S_pad;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+            raw[u][v] = HINT ? ld_nc_hint(rowp + offs[v], pol_keep) : __ldg(reinterpret_cast<const uint4 *>(rowp + offs[v]));
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+        const float w = weighted ? __shfl_sync(gmask, wl, q0 + u, G) : 1.0f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            if (!weighted) {
+                VecT<T>::add_to(raw[u][v], Y[v]);
+            } else {
+                float xv[VEC];
+                VecT<T>::unpack(raw[u][v], xv);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, xv[e], Y[v][e]);
+            }
+        }
+    }
+}
+
+// Y = sum of the neighbour rows of a row whose indices start in `x`.
+// Neighbours go in batches of UNR whose loads are all in flight together (a
+// short row costs one round trip to L2); the last, shorter batch takes
+// straight-line code for its exact length. HINT: loads carry the L2 policy
+// pol_keep.
+template <typename T, int G, int VPL, bool HINT = false>
+__device__ __forceinline__ void gather_row(const InstDesc *__restrict__ d, const T *__restrict__ Xc, const RowIdx &x,
+                                           int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
+                                           float &dsum, uint64_t pol_keep = 0)
+{
+    constexpr int VEC = VecT<T>::N;
+    constexpr int UNR = VPL >= 4 ? 2 : 4;   // neighbours in flight per batch
     const int32_t *__restrict__ colp = d->col;
     const int32_t *__restrict__ wp = d->w;
+    const bool weighted = wp != nullptr;
     // this lane's column offsets; lanes past the padded row read column 0 and discard it
     int offs[VPL];
     bool inr[VPL];
@@ -169,43 +223,33 @@ __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, co
         inr[v] = offs[v] < S_pad;
         if (!inr[v]) offs[v] = 0;
     }
-    if (wp == nullptr) dsum = (float)(k1 - k0);
-    for (int kb = k0; kb < k1; kb += G) {
-        const int myk = kb + gl;
-        int jl = 0;
-        float wl = 0.0f;
-        if (myk < k1) {
-            jl = __ldg(colp + myk);
-            wl = wp ? (float)__ldg(wp + myk) : 1.0f;
+    if (!weighted) dsum = (float)(x.k1 - x.k0);
+    int jl = x.jl;
+    float wl = x.wl;
+    for (int kb = x.k0; kb < x.k1; kb += G) {
+        if (kb != x.k0) {   // later batches of a long row load their indices here
+            const int myk = kb + gl;
+            jl = 0;
+            wl = 0.0f;
+            if (myk < x.k1) {
+                jl = __ldg(colp + myk);
+                wl = weighted ? (float)__ldg(wp + myk) : 1.0f;
+            }
         }
-        if (wp) dsum += group_sum<G>(wl, gmask);
-        const int cnt = min(G, k1 - kb);
-        for (int q = 0; q < cnt; q += UNR) {
-            uint4 raw[UNR][VPL];   // packed until accumulated: 4 registers per 16-byte slice
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const T *rowp = Xc + (size_t)__shfl_sync(gmask, jl, q + u, G) * S_pad;
-#pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    raw[u][v] = make_uint4(0u, 0u, 0u, 0u);
-                    if (q + u < cnt) raw[u][v] = __ldg(reinterpret_cast<const uint4 *>(rowp + offs[v]));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-#pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    if (wp == nullptr) {
-                        VecT<T>::add_to(raw[u][v], Y[v]);
-                    } else {
-                        const float w = __shfl_sync(gmask, wl, q + u, G);
-                        float x[VEC];
-                        VecT<T>::unpack(raw[u][v], x);
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) Y[v][e] = fmaf(w, x[e], Y[v][e]);
-                    }
-                }
-            }
+        if (weighted) dsum += group_sum<G>(wl, gmask);
+        const int cnt = min(G, x.k1 - kb);
+        int q = 0;
+        for (; q + UNR <= cnt; q += UNR)
+            gather_batch<T, G, VPL, UNR, HINT>(Xc, jl, wl, q, weighted, offs, S_pad, gmask, Y, pol_keep);
+        switch (cnt - q) {   // group-uniform
+            case 1: gather_batch<T, G, VPL, 1, HINT>(Xc, jl, wl, q, weighted, offs, S_pad, gmask, Y, pol_keep); break;
+            case 2:
+                if (UNR > 2) gather_batch<T, G, VPL, 2, HINT>(Xc, jl, wl, q, weighted, offs, S_pad, gmask, Y, pol_keep);
+                break;
+            case 3:
+                if (UNR > 3) gather_batch<T, G, VPL, 3, HINT>(Xc, jl, wl, q, weighted, offs, S_pad, gmask, Y, pol_keep);
+                break;
+            default: break;
         }
     }
 #pragma unroll
@@ -214,6 +258,15 @@ __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, co
 #pragma unroll
             for (int e = 0; e < VEC; ++e) Y[v][e] = 0.0f;
         }
+}
+
+// Direct gather of the whole neighbour list of `row` from global memory.
+template <typename T, int G, int VPL>
+__device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, const T *__restrict__ Xc, int row,
+                                              int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
+                                              float &dsum)
+{
+    gather_row<T, G, VPL>(d, Xc, load_row_idx(d, row, gl), S_pad, gl, gmask, Y, dsum);
 }
 
 // The row's own data: p (FP32 master or state), the AdamW moments, and the
@@ -256,12 +309,12 @@ __device__ __forceinline__ void load_own(const InstDesc *__restrict__ d, const S
 
 // Everything after the sparse product for one row: statistics, gradient,
 // AdamW, noise, clamp, stores (and the clique partial column sums).
-template <typename T, int G, int VPL>
+template <typename T, int G, int VPL, bool HINT = false>
 __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
                                            unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
                                            const OwnRow<T, G, VPL> &o, RunStatus *__restrict__ status,
                                            float *colsum_acc, float *pn_out = nullptr,
-                                           const float2 *pre_stats = nullptr)
+                                           const float2 *pre_stats = nullptr, L2Policies pol = L2Policies{0, 0})
 {
     constexpr int VEC = VecT<T>::N;
     T *__restrict__ Xn = reinterpret_cast<T *>(d->X[(c.t + 1) & 1]);
@@ -272,6 +325,22 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     if (c.alpha != 0.0f && pre_stats) {   // row statistics computed earlier by the caller
         mean = pre_stats->x;
         inv_std = pre_stats->y;
+    } else if (c.alpha != 0.0f && c.S == G * VPL * VEC) {   // every lane's vectors are all replicas
+        float sum = 0.0f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) sum += o.P[v][e];
+        mean = group_sum<G>(sum, gmask) * c.inv_S;
+        float sq = 0.0f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float dl = o.P[v][e] - mean;
+                sq = fmaf(dl, dl, sq);
+            }
+        inv_std = rsqrt_ftz(group_sum<G>(sq, gmask) * c.inv_S + c.comm_eps);
     } else if (c.alpha != 0.0f) {
         float sum = 0.0f;
 #pragma unroll
@@ -386,14 +455,25 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
         // p, m and v enter finite (the state is checked on the way in), so any
         // NaN, Inf or overflow of the gradient shows in the second moment
         if (!(vsum <= 3.0e38f)) atomicAdd(&status->nonfinite, 1ULL);
-        VecT<T>::store(Xn + rbase + off, pn);
-        if (d->master) {
-            for (int k = 0; k < VEC; k += 4)
-                *reinterpret_cast<float4 *>(d->master + rbase + off + k) =
-                    make_float4(pn[k], pn[k + 1], pn[k + 2], pn[k + 3]);
+        if (HINT) {
+            st_hint(Xn + rbase + off, VecT<T>::pack(pn), pol.keep);
+            if (d->master) {
+#pragma unroll
+                for (int k = 0; k < VEC; k += 4)
+                    st_hint(d->master + rbase + off + k, VecT<float>::pack(pn + k), pol.stream);
+            }
+            st_hint(reinterpret_cast<T *>(d->m) + rbase + off, VecT<T>::pack(M), pol.stream);
+            st_hint(reinterpret_cast<T *>(d->v) + rbase + off, VecT<T>::pack(V), pol.stream);
+        } else {
+            VecT<T>::store(Xn + rbase + off, pn);
+            if (d->master) {
+                for (int k = 0; k < VEC; k += 4)
+                    *reinterpret_cast<float4 *>(d->master + rbase + off + k) =
+                        make_float4(pn[k], pn[k + 1], pn[k + 2], pn[k + 3]);
+            }
+            VecT<T>::store(reinterpret_cast<T *>(d->m) + rbase + off, M);
+            VecT<T>::store(reinterpret_cast<T *>(d->v) + rbase + off, V);
         }
-        VecT<T>::store(reinterpret_cast<T *>(d->m) + rbase + off, M);
-        VecT<T>::store(reinterpret_cast<T *>(d->v) + rbase + off, V);
         if (c.kind == kMaxClique) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) atomicAdd(colsum_acc + off + e, pn[e]);
@@ -496,6 +576,17 @@ __device__ __forceinline__ void tma_bulk_load(void *dst, const void *src, uint32
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(mbar))
                  : "memory");
+}
+
+// The same with an L2 cache policy for the source reads.
+__device__ __forceinline__ void tma_bulk_load_hint(void *dst, const void *src, uint32_t bytes, uint64_t *mbar,
+                                                   uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar)), "l"(pol)
+        : "memory");
 }
 
 // Wait for phase `parity` of mbar with a clock limit; false if it ran out.
@@ -759,7 +850,10 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     // header: two barriers per warp (at most 8 warps); then each warp's two buffers
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw) + 2 * warp;
     unsigned char *const buf0 = smem_raw + 128 + (size_t)warp * 2 * buf_bytes;   // buffer b at buf0 + b * buf_bytes
-    const int num_tiles = *num_tiles_p;
+    const int num_tiles = num_tiles_p[0];
+    // num_tiles_p[1] != 0: the run's state does not fit in L2, so the streamed
+    // slabs are read and written evict-first and p is kept (evict-last)
+    const L2Policies pol = make_l2_policies(num_tiles_p[1] != 0);
     const int W = gridDim.x * nwarps;
     const int first = blockIdx.x * nwarps + warp;
 
@@ -770,10 +864,9 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     }
     __syncwarp();
 
-    // Lane 0 only: start the copies of `tile`'s slabs into buffer b (nothing for
-    // a finished instance, whose tile the warp skips). Returns whether it did.
-    auto issue = [&](int tile, int b) -> bool {
-        const Tile tl = tiles[tile];
+    // Lane 0 only: start the copies of tile tl's slabs into buffer b (nothing
+    // for a finished instance, whose tile the warp skips). Returns whether it did.
+    auto issue = [&](const Tile &tl, int b) -> bool {
         const InstDesc *__restrict__ d = descs + tl.slot;
         const int t = d->t + r;
         if (t >= d->K) return false;
@@ -787,26 +880,53 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         const size_t vofs = mofs + (size_t)R * d->S_pad * sizeof(T);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&mbar[b], pbytes + 2 * sbytes);
-        tma_bulk_load(dst, psrc, pbytes, &mbar[b]);
-        tma_bulk_load(dst + mofs, reinterpret_cast<const T *>(d->m) + e0, sbytes, &mbar[b]);
-        tma_bulk_load(dst + vofs, reinterpret_cast<const T *>(d->v) + e0, sbytes, &mbar[b]);
+        // (FP32 runs read p^t itself here; it is gathered too, so it is kept)
+        tma_bulk_load_hint(dst, psrc, pbytes, &mbar[b], d->master ? pol.stream : pol.keep);
+        tma_bulk_load_hint(dst + mofs, reinterpret_cast<const T *>(d->m) + e0, sbytes, &mbar[b], pol.stream);
+        tma_bulk_load_hint(dst + vofs, reinterpret_cast<const T *>(d->v) + e0, sbytes, &mbar[b], pol.stream);
         return true;
     };
+
+    // Software pipeline over the warp's tiles: tile records are fetched two
+    // tiles ahead, the row bounds and first neighbour indices one tile ahead,
+    // and the slabs one tile ahead, so a tile's only exposed latency is the
+    // gather of its neighbour rows.
+    const Tile none{0, 0};
+    Tile tl_cur = first < num_tiles ? tiles[first] : none;
+    Tile tl_nxt = first + W < num_tiles ? tiles[first + W] : none;
+    RowIdx ix_cur = first < num_tiles ? load_row_idx(descs + tl_cur.slot, tl_cur.row0 + grp, gl) : RowIdx{0, 0, 0, 0.0f};
 
     // completed phases of each buffer's barrier (warp-uniform), and lane 0's
     // record of a copy in flight into the buffer not being read
     uint32_t uses0 = 0u, uses1 = 0u;
     bool next_pending = false;
     int b = 0;
-    if (lane == 0 && first < num_tiles) issue(first, 0);
+    // the step context of the instance of the previous tile (most consecutive
+    // tiles of a warp belong to the same instance)
+    int ctx_slot = -1;
+    StepCtx c{};
+    if (lane == 0 && first < num_tiles) issue(tl_cur, 0);
     for (int tile = first; tile < num_tiles; tile += W, b ^= 1) {
+        const bool has_next = tile + W < num_tiles;
         // buffer b^1 was last read in the previous iteration, which ended in __syncwarp
-        if (lane == 0) next_pending = tile + W < num_tiles && issue(tile + W, b ^ 1);
-        const Tile tl = tiles[tile];
+        if (lane == 0) next_pending = has_next && issue(tl_nxt, b ^ 1);
+        RowIdx ix_nxt{0, 0, 0, 0.0f};
+        if (has_next) ix_nxt = load_row_idx(descs + tl_nxt.slot, tl_nxt.row0 + grp, gl);
+        const Tile tl_nn = tile + 2 * W < num_tiles ? tiles[tile + 2 * W] : none;
+
+        const Tile tl = tl_cur;
+        const RowIdx ix = ix_cur;
+        tl_cur = tl_nxt;
+        tl_nxt = tl_nn;
+        ix_cur = ix_nxt;
         const InstDesc *__restrict__ d = descs + tl.slot;
-        const int t = d->t + r;
-        if (t >= d->K) continue;   // finished instance: no copy was issued, nothing is read
-        const StepCtx c = make_ctx(d, t, r);
+        if (tl.slot != ctx_slot) {
+            const int t = d->t + r;
+            if (t >= d->K) continue;   // finished instance: no copy was issued, nothing is read
+            c = make_ctx(d, t, r);
+            ctx_slot = tl.slot;
+        }
+        const int t = c.t;
         const bool clique = (c.kind == kMaxClique);
         if (clique && tl.row0 == 0) {   // zero the column sums step t+1 accumulates into
             float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
@@ -820,7 +940,8 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
             for (int e = 0; e < VecT<T>::N; ++e) Y[v][e] = 0.0f;
         float dsum = 0.0f;
         if (row < c.n)
-            gather_direct<T, G, VPL>(d, reinterpret_cast<const T *>(d->X[t & 1]), row, c.S_pad, gl, gmask, Y, dsum);
+            gather_row<T, G, VPL, true>(d, reinterpret_cast<const T *>(d->X[t & 1]), ix, c.S_pad, gl, gmask, Y, dsum,
+                                        pol.keep);
         const uint32_t parity = (b ? uses1 : uses0) & 1u;
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[b], parity));
         if (!ok) {
@@ -838,7 +959,7 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         if (row < c.n) {
             OwnRow<T, G, VPL> own;
             load_own_smem<T, G, VPL>(buf0 + (size_t)b * buf_bytes, R, c.S_pad, grp, gl, own);
-            update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status, c.cs_next);
+            update_row<T, G, VPL, true>(d, c, row, gl, gmask, Y, dsum, own, status, c.cs_next, nullptr, nullptr, pol);
         }
         __syncwarp();   // every lane is done with buffer b
     }

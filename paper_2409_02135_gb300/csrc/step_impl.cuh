@@ -272,10 +272,50 @@ __device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, co
 // The row's own data: p (FP32 master or state), the AdamW moments, and the
 // clique column sums. Loaded before the sparse product where registers allow,
 // so their latency overlaps the neighbour gathers.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 template <typename T, int G, int VPL>
 struct OwnRow {
     float P[VPL][VecT<T>::N];
     uint4 M[VPL], V[VPL];   // raw 16-byte storage vectors, unpacked when used
+    static constexpr bool kLean = false;   // the whole row is in registers
+    __device__ __forceinline__ void load_p(int v, float (&out)[VecT<T>::N]) const
+    {
+#pragma unroll
+        for (int e = 0; e < VecT<T>::N; ++e) out[e] = P[v][e];
+    }
+    __device__ __forceinline__ uint4 mraw(int v) const { return M[v]; }
+    __device__ __forceinline__ uint4 vraw(int v) const { return V[v]; }
+};
+
+// The same row read from shared memory each time a vector is used, so only
+// one vector of it occupies registers at a time.
+template <typename T, int G, int VPL>
+struct OwnSmem {
+    const float *sP;   // this row's p in shared memory
+    const T *sM, *sV;  // this row's m, v in shared memory
+    int gl;
+    static constexpr bool kLean = true;
+    __device__ __forceinline__ void load_p(int v, float (&out)[VecT<T>::N]) const
+    {
+        const float *q = sP + (v * G + gl) * VecT<T>::N;
+#pragma unroll
+        for (int k = 0; k < VecT<T>::N; k += 4) {
+            float4 a;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
+                         : "r"(smem_addr(q + k)));
+            out[k] = a.x; out[k + 1] = a.y; out[k + 2] = a.z; out[k + 3] = a.w;
+        }
+    }
+    __device__ __forceinline__ static uint4 lds16(const void *q)
+    {
+        uint4 a;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w) : "r"(smem_addr(q)));
+        return a;
+    }
+    __device__ __forceinline__ uint4 mraw(int v) const { return lds16(sM + (v * G + gl) * VecT<T>::N); }
+    __device__ __forceinline__ uint4 vraw(int v) const { return lds16(sV + (v * G + gl) * VecT<T>::N); }
 };
 
 template <typename T, int G, int VPL>
@@ -309,10 +349,10 @@ __device__ __forceinline__ void load_own(const InstDesc *__restrict__ d, const S
 
 // Everything after the sparse product for one row: statistics, gradient,
 // AdamW, noise, clamp, stores (and the clique partial column sums).
-template <typename T, int G, int VPL, bool HINT = false>
+template <typename T, int G, int VPL, bool HINT = false, typename Own = OwnRow<T, G, VPL>>
 __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
                                            unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
-                                           const OwnRow<T, G, VPL> &o, RunStatus *__restrict__ status,
+                                           const Own &o, RunStatus *__restrict__ status,
                                            float *colsum_acc, float *pn_out = nullptr,
                                            const float2 *pre_stats = nullptr, L2Policies pol = L2Policies{0, 0})
 {
@@ -328,31 +368,39 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     } else if (c.alpha != 0.0f && c.S == G * VPL * VEC) {   // every lane's vectors are all replicas
         float sum = 0.0f;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v)
+        for (int v = 0; v < VPL; ++v) {
+            float P[VEC];
+            o.load_p(v, P);
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) sum += o.P[v][e];
+            for (int e = 0; e < VEC; ++e) sum += P[e];
+        }
         mean = group_sum<G>(sum, gmask) * c.inv_S;
         float sq = 0.0f;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v)
+        for (int v = 0; v < VPL; ++v) {
+            float P[VEC];
+            o.load_p(v, P);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                const float dl = o.P[v][e] - mean;
+                const float dl = P[e] - mean;
                 sq = fmaf(dl, dl, sq);
             }
+        }
         inv_std = rsqrt_ftz(group_sum<G>(sq, gmask) * c.inv_S + c.comm_eps);
     } else if (c.alpha != 0.0f) {
         float sum = 0.0f;
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             const int nv = c.S - (v * G + gl) * VEC;   // valid replicas in this vector
+            float P[VEC];
+            o.load_p(v, P);
             if (nv >= VEC) {
 #pragma unroll
-                for (int e = 0; e < VEC; ++e) sum += o.P[v][e];
+                for (int e = 0; e < VEC; ++e) sum += P[e];
             } else {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e)
-                    if (e < nv) sum += o.P[v][e];
+                    if (e < nv) sum += P[e];
             }
         }
         mean = group_sum<G>(sum, gmask) * c.inv_S;
@@ -360,9 +408,11 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             const int nv = c.S - (v * G + gl) * VEC;
+            float P[VEC];
+            o.load_p(v, P);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                const float dl = o.P[v][e] - mean;
+                const float dl = P[e] - mean;
                 if (nv >= VEC || e < nv) sq = fmaf(dl, dl, sq);
             }
         }
@@ -376,8 +426,9 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     const float om_b1 = 1.0f - c.b1, om_b2 = 1.0f - c.b2;
 
     // Langevin noise: all of the lane's replica quads in one lockstep Philox
-    // pass when they fit in 16 registers, else one pass per vector
-    constexpr bool kRowNoise = VPL * VEC <= 16;
+    // pass when they fit in 16 registers (and the row is held in registers),
+    // else one pass per vector
+    constexpr bool kRowNoise = VPL * VEC <= 16 && !Own::kLean;
     float xi_row[kRowNoise ? VPL : 1][VEC];
     if (kRowNoise) {
         uint32_t qs[VPL * VEC / 4];
@@ -394,6 +445,8 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     for (int v = 0; v < VPL; ++v) {
         const int off = (v * G + gl) * VEC;
         if (off >= c.S_pad) continue;
+        float P[VEC];
+        o.load_p(v, P);
         float g[VEC];
         if (c.kind == kMaxClique) {   // Eq. 24, column sums of the previous step
 #pragma unroll
@@ -406,13 +459,13 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
         if (c.half_pow == 1) {   // a = 4, the paper's exponent
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                const float u = fmaf(2.0f, o.P[v][e], -1.0f);
+                const float u = fmaf(2.0f, P[e], -1.0f);
                 g[e] = fmaf(c.ent_coef, u * (u * u), g[e]);
             }
         } else {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) {
-                const float u = fmaf(2.0f, o.P[v][e], -1.0f);
+                const float u = fmaf(2.0f, P[e], -1.0f);
                 const float u2 = u * u;
                 float upow = u;
                 for (int k = 0; k < c.half_pow; ++k) upow *= u2;
@@ -421,7 +474,7 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
         }
         // cross-replica communication (Eq. 10)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) g[e] = fmaf(comm_coef, o.P[v][e] - mean, g[e]);
+        for (int e = 0; e < VEC; ++e) g[e] = fmaf(comm_coef, P[e] - mean, g[e]);
         if (c.grad_dbg) {
 #pragma unroll
             for (int e = 0; e < VEC; ++e) c.grad_dbg[rbase + off + e] = g[e];
@@ -435,8 +488,8 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
         }
         const float *xi = kRowNoise ? xi_row[kRowNoise ? v : 0] : xi_vec;
         float pn[VEC], M[VEC], V[VEC];
-        VecT<T>::unpack(o.M[v], M);
-        VecT<T>::unpack(o.V[v], V);
+        VecT<T>::unpack(o.mraw(v), M);
+        VecT<T>::unpack(o.vraw(v), V);
         float vsum = 0.0f;
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
@@ -445,7 +498,7 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
             const float mn = fmaf(c.b1, M[e], om_b1 * g[e]);
             const float vn = fmaf(c.b2, V[e], om_b2 * (g[e] * g[e]));
             const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
-            float q = o.P[v][e] * c.decay;
+            float q = P[e] * c.decay;
             q = fmaf(-c.step_size, mn * rcp_ftz(denom), q);
             pn[e] = __saturatef(fmaf(c.noise_scale, xi[e], q));
             vsum += vn;
@@ -542,7 +595,6 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
 // neighbour index) and every row consumes, per chunk, the prefix of its
 // remaining (sorted) neighbour list that falls inside the chunk.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count)
 {
@@ -957,8 +1009,10 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         }
         if (b) ++uses1; else ++uses0;
         if (row < c.n) {
-            OwnRow<T, G, VPL> own;
-            load_own_smem<T, G, VPL>(buf0 + (size_t)b * buf_bytes, R, c.S_pad, grp, gl, own);
+            const unsigned char *bb = buf0 + (size_t)b * buf_bytes;
+            const T *sM = reinterpret_cast<const T *>(bb + (size_t)R * c.S_pad * sizeof(float)) + (size_t)grp * c.S_pad;
+            const OwnSmem<T, G, VPL> own{reinterpret_cast<const float *>(bb) + (size_t)grp * c.S_pad, sM,
+                                          sM + (size_t)R * c.S_pad, gl};
             update_row<T, G, VPL, true>(d, c, row, gl, gmask, Y, dsum, own, status, c.cs_next, nullptr, nullptr, pol);
         }
         __syncwarp();   // every lane is done with buffer b

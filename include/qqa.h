@@ -161,7 +161,7 @@ void qqa_destroy_problem(qqa_problem *p);
 
 /* ----------------------------------------------------------------- runs */
 /*
- * Create a run with room for `capacity` instances whose replica counts are at
+ * Create a run with room for `capacity` (1..65535) instances whose replica counts are at
  * most S_max, all in `precision`. No instance is active yet. The step kernel
  * layout is fixed here from (S_max, precision, cfg); cfg may be NULL.
  * Device memory of the state is allocated per instance by qqa_run_add.

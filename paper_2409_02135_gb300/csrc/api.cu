@@ -513,7 +513,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
 {
     if (!out) return fail(QQA_EINVAL, "out is NULL");
     *out = nullptr;
-    if (capacity < 1) return fail(QQA_EINVAL, "capacity must be >= 1");
+    if (capacity < 1 || capacity > 65535) return fail(QQA_EINVAL, "capacity must be in [1, 65535] (got %d)", capacity);
     if (precision != QQA_FP32 && precision != QQA_BF16) return fail(QQA_EINVAL, "unknown precision %d", precision);
     if (S_max < 1 || S_max > 1024) return fail(QQA_EINVAL, "S_max must be in [1, 1024] (got %d)", S_max);
     cudaStream_t st = (cudaStream_t)stream;
@@ -966,9 +966,15 @@ extern "C" int qqa_run_eval(qqa_run *r, void *stream)
     if (!r) return fail(QQA_EINVAL, "run is NULL");
     if (r->num_tiles == 0) return QQA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int32_t grid = std::min(r->num_tiles, 65535);
-    launch_eval(r->d_descs, r->d_tiles, r->d_num_tiles, grid, r->rows_per_tile, r->capacity, r->S_max_pad, r->prec, st);
-    g_launches += 3;
+    int32_t n_max = 0;
+    int64_t total_rows = 0;
+    for (const auto &s : r->slots)
+        if (s.active) {
+            n_max = std::max(n_max, s.n);
+            total_rows += s.n;
+        }
+    launch_eval(r->d_descs, r->capacity, n_max, total_rows, r->S_max_pad, r->prec, st);
+    g_launches += 5;
     QQA_CK_LAUNCH("eval");
     for (auto &s : r->slots)
         if (s.active && s.t != s.last_eval_t) s.last_eval_t = s.t;

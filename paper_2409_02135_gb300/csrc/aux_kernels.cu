@@ -1,6 +1,8 @@
 // aux_kernels.cu -- everything around the fused step: initial state, the
 // clique column sums, step-counter advance, projection rounding with exact
 // integer costs, and state import/export for checkpoints and tests.
+#include <algorithm>
+
 #include "qqa_internal.cuh"
 
 namespace qqa {
@@ -130,97 +132,96 @@ __device__ __forceinline__ float state_value(const InstDesc &d, size_t e, int32_
     return prec == kFP32 ? reinterpret_cast<const float *>(d.X[d.t & 1])[e] : d.master[e];
 }
 
-// Evaluation work items: each step tile is split into `sub` pieces of
-// `rows_per_item` rows, so the evaluation keeps the GPU busy even when the
-// step kernel uses tall tiles.
-// bits[i][w] bit b = (p[i][32w+b] > 1/2) for 32w+b < S; zero the cost counters.
-__global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
-                                 const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t sub,
-                                 int32_t rows_per_item, int32_t prec)
+// The evaluation runs on its own grid: blockIdx.y is the slot, blockIdx.x a
+// chunk of `rows` consecutive rows of it (independent of the step kernel's
+// tiles, which may be a few rows high).
+//
+// bits[i][w] bit b = (p[i][32w+b] > 1/2) for 32w+b < S; the first chunk of a
+// slot zeroes its cost counters.
+__global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, int32_t rows, int32_t prec)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int items = *num_tiles_p * sub;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const Tile tl = tiles[item / sub];
-        const int part = item % sub;
-        const InstDesc &d = descs[tl.slot];
-        if (!needs_eval(d)) continue;
-        if (tl.row0 == 0 && part == 0)
-            for (int k = threadIdx.x; k < 3 * d.S_pad; k += blockDim.x) d.counts[k] = 0ULL;
-        const int r0 = tl.row0 + part * rows_per_item;
-        const int rows = min(min(rows_per_item, tl.row0 + rows_per_tile - r0), d.n - r0);
-        if (rows <= 0) continue;
-        const int pairs = rows * d.W;
-        for (int pidx = warp; pidx < pairs; pidx += nwarps) {
-            const int i = r0 + pidx / d.W;
-            const int w = pidx % d.W;
-            const int s = 32 * w + lane;
-            const bool x = s < d.S && state_value(d, (size_t)i * d.S_pad + s, prec) > 0.5f;
-            const unsigned word = __ballot_sync(0xffffffffu, x);
-            if (lane == 0) d.bits[(size_t)i * d.W + w] = word;
-        }
+    const InstDesc &d = descs[blockIdx.y];
+    if (!needs_eval(d)) return;
+    const int r0 = blockIdx.x * rows;
+    if (r0 >= d.n) return;
+    if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < 3 * d.S_pad; k += blockDim.x) d.counts[k] = 0ULL;
+    const int nr = min(rows, d.n - r0);
+    const int pairs = nr * d.W;
+    for (int pidx = warp; pidx < pairs; pidx += nwarps) {
+        const int i = r0 + pidx / d.W;
+        const int w = pidx % d.W;
+        const int s = 32 * w + lane;
+        const bool x = s < d.S && state_value(d, (size_t)i * d.S_pad + s, prec) > 0.5f;
+        const unsigned word = __ballot_sync(0xffffffffu, x);
+        if (lane == 0) d.bits[(size_t)i * d.W + w] = word;
     }
 }
 
 // Per replica: size = sum x_i, inside = #edges (i<j) with x_i x_j, cut = sum w_ij [x_i != x_j].
-// One block per tile: the tile's (row, replica) items are spread over all
-// threads (threads sharing a replica split the rows), partial counts are
-// combined in shared memory, then added to the slot's counters.
-__global__ void eval_count_kernel(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
-                                  const int32_t *__restrict__ num_tiles_p, int32_t rows_per_tile, int32_t sub,
-                                  int32_t rows_per_item)
+// Threads sharing a replica split the chunk's rows; each walks its rows'
+// neighbour lists eight entries at a time with the index and bit-word loads
+// of a batch in flight together. Partial counts are combined in shared
+// memory, then added to the slot's counters.
+__global__ void eval_count_kernel(const InstDesc *__restrict__ descs, int32_t rows)
 {
     extern __shared__ long long sh_cnt[];   // [3][S_pad32]
-    const int items = *num_tiles_p * sub;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const Tile tl = tiles[item / sub];
-        const int r0 = tl.row0 + (item % sub) * rows_per_item;
-        const InstDesc &d = descs[tl.slot];
-        if (!needs_eval(d)) continue;
-        const int row_end = min(min(r0 + rows_per_item, tl.row0 + rows_per_tile), d.n);
-        if (r0 >= row_end) continue;   // block-uniform
-        const int S32 = (d.S + 31) & ~31;
-        for (int k = threadIdx.x; k < 3 * S32; k += blockDim.x) sh_cnt[k] = 0;
-        __syncthreads();
-        const int splits = max(1, (int)blockDim.x / S32);
-        for (int base = threadIdx.x; base < splits * S32; base += blockDim.x) {
-            const int s = base % S32;
-            const int part = base / S32;
-            if (s >= d.S) continue;
-            const int w = s >> 5;
-            const int b = s & 31;
-            long long size = 0, inside = 0, cut = 0;
-            for (int i = r0 + part; i < row_end; i += splits) {
-                const unsigned xi = (d.bits[(size_t)i * d.W + w] >> b) & 1u;
-                size += xi;
-                const int k1 = d.row_ptr[i + 1];
-                for (int k = d.row_ptr[i]; k < k1; ++k) {
-                    const int j = d.col[k];
-                    if (j <= i) continue;   // each undirected edge once
-                    const unsigned xj = (d.bits[(size_t)j * d.W + w] >> b) & 1u;
+    const InstDesc &d = descs[blockIdx.y];
+    if (!needs_eval(d)) return;
+    const int r0 = blockIdx.x * rows;
+    if (r0 >= d.n) return;   // block-uniform
+    const int row_end = min(r0 + rows, d.n);
+    const int S32 = (d.S + 31) & ~31;
+    for (int k = threadIdx.x; k < 3 * S32; k += blockDim.x) sh_cnt[k] = 0;
+    __syncthreads();
+    const int splits = max(1, (int)blockDim.x / S32);
+    const int32_t *__restrict__ col = d.col;
+    const int32_t *__restrict__ wts = d.w;
+    const uint32_t *__restrict__ bits = d.bits;
+    for (int base = threadIdx.x; base < splits * S32; base += blockDim.x) {
+        const int s = base % S32;
+        const int part = base / S32;
+        if (s >= d.S) continue;
+        const int w = s >> 5;
+        const int b = s & 31;
+        long long size = 0, inside = 0, cut = 0;
+        for (int i = r0 + part; i < row_end; i += splits) {
+            const unsigned xi = (bits[(size_t)i * d.W + w] >> b) & 1u;
+            size += xi;
+            const int k1 = d.row_ptr[i + 1];
+            for (int k = d.row_ptr[i]; k < k1; k += 8) {
+                int j[8];
+                unsigned word[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) j[u] = k + u < k1 ? __ldg(col + k + u) : -1;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) word[u] = j[u] > i ? __ldg(bits + (size_t)j[u] * d.W + w) : 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (j[u] <= i) continue;   // each undirected edge once (and past the row's end)
+                    const unsigned xj = (word[u] >> b) & 1u;
                     inside += (long long)(xi & xj);
-                    if (xi != xj) cut += d.w ? (long long)d.w[k] : 1LL;
+                    if (xi != xj) cut += wts ? (long long)__ldg(wts + k + u) : 1LL;
                 }
             }
-            if (size) atomicAdd((unsigned long long *)&sh_cnt[s], (unsigned long long)size);
-            if (inside) atomicAdd((unsigned long long *)&sh_cnt[S32 + s], (unsigned long long)inside);
-            if (cut) atomicAdd((unsigned long long *)&sh_cnt[2 * S32 + s], (unsigned long long)cut);
         }
-        __syncthreads();
-        for (int s = threadIdx.x; s < d.S; s += blockDim.x) {
-            if (sh_cnt[s]) atomicAdd(&d.counts[s], (unsigned long long)sh_cnt[s]);
-            if (sh_cnt[S32 + s]) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)sh_cnt[S32 + s]);
-            if (sh_cnt[2 * S32 + s]) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)sh_cnt[2 * S32 + s]);
-        }
-        __syncthreads();
+        if (size) atomicAdd((unsigned long long *)&sh_cnt[s], (unsigned long long)size);
+        if (inside) atomicAdd((unsigned long long *)&sh_cnt[S32 + s], (unsigned long long)inside);
+        if (cut) atomicAdd((unsigned long long *)&sh_cnt[2 * S32 + s], (unsigned long long)cut);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < d.S; s += blockDim.x) {
+        if (sh_cnt[s]) atomicAdd(&d.counts[s], (unsigned long long)sh_cnt[s]);
+        if (sh_cnt[S32 + s]) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)sh_cnt[S32 + s]);
+        if (sh_cnt[2 * S32 + s]) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)sh_cnt[2 * S32 + s]);
     }
 }
 
 // One warp per slot: objective, violation, feasibility, energy of every
-// replica; best feasible replica (max objective, ties -> lowest s); history;
-// bit-packed x of the best replica.
+// replica; best feasible replica (max objective, ties -> lowest s); history.
 __global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32_t capacity)
 {
     InstDesc *descs = const_cast<InstDesc *>(descs_c);
@@ -262,13 +263,6 @@ __global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32
         const bool take = s2 >= 0 && (best_s < 0 || o2 > best_obj || (o2 == best_obj && s2 < best_s));
         if (take) { best_obj = o2; best_s = s2; }
     }
-    for (int base = 0; base < d.n; base += 32) {
-        const int i = base + lane;
-        unsigned bit = 0;
-        if (i < d.n && best_s >= 0) bit = (d.bits[(size_t)i * d.W + (best_s >> 5)] >> (best_s & 31)) & 1u;
-        const unsigned word = __ballot_sync(0xffffffffu, bit != 0);
-        if (lane == 0) d.res_bestx[base >> 5] = word;
-    }
     if (lane == 0) {
         const int count = d.res_meta[2];
         d.res_meta[0] = best_s;
@@ -278,22 +272,54 @@ __global__ void eval_finalize_kernel(const InstDesc *__restrict__ descs_c, int32
             d.hist_step[count] = d.t;
         }
         d.res_meta[2] = count + 1;
-        d.last_eval_t = d.t;
     }
 }
 
-void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
-                 int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st)
+// Bit-packed x of the best replica: one warp per 32 nodes, over the same
+// (chunk, slot) grid as the counting kernels.
+__global__ void eval_bestx_kernel(const InstDesc *__restrict__ descs, int32_t rows)
 {
-    const int rows_per_item = 8;
-    const int sub = (rows_per_tile + rows_per_item - 1) / rows_per_item;
-    const long long items = (long long)grid * sub;   // grid = number of tiles when launched
-    const int g = (int)(items < 65535 ? items : 65535);
-    eval_bits_kernel<<<g, 256, 0, st>>>(descs, tiles, num_tiles, rows_per_tile, sub, rows_per_item, prec);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const InstDesc &d = descs[blockIdx.y];
+    if (!needs_eval(d)) return;
+    const int best_s = d.res_meta[0];
+    const int w0 = blockIdx.x * (rows >> 5);
+    const int nwords = (d.n + 31) >> 5;
+    for (int word = w0 + warp; word < min(w0 + (rows >> 5), nwords); word += blockDim.x >> 5) {
+        const int i = (word << 5) + lane;
+        unsigned bit = 0;
+        if (i < d.n && best_s >= 0) bit = (d.bits[(size_t)i * d.W + (best_s >> 5)] >> (best_s & 31)) & 1u;
+        const unsigned packed = __ballot_sync(0xffffffffu, bit != 0);
+        if (lane == 0) d.res_bestx[word] = packed;
+    }
+}
+
+// The evaluation of step t is complete: later evaluations at the same t are skipped.
+__global__ void eval_mark_kernel(InstDesc *__restrict__ descs, int32_t capacity)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot < capacity && needs_eval(descs[slot])) descs[slot].last_eval_t = descs[slot].t;
+}
+
+void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
+                 int32_t prec, cudaStream_t st)
+{
+    // rows per counting chunk: a multiple of 8, small enough for about four
+    // waves of 256-thread blocks (8 per SM) over the whole run
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int rows = (int)std::min<int64_t>(256, std::max<int64_t>(8, total_rows / (32LL * sms)));
+    rows = (rows + 7) & ~7;
+    const dim3 grid(std::max(1, (n_max + rows - 1) / rows), capacity);
+    eval_bits_kernel<<<grid, 256, 0, st>>>(descs, rows, prec);
     const int S32 = (S_max_pad + 31) & ~31;
-    eval_count_kernel<<<g, 256, 3 * S32 * sizeof(long long), st>>>(descs, tiles, num_tiles, rows_per_tile, sub,
-                                                                   rows_per_item);
+    eval_count_kernel<<<grid, 256, 3 * S32 * sizeof(long long), st>>>(descs, rows);
     eval_finalize_kernel<<<(capacity + 7) / 8, 256, 0, st>>>(descs, capacity);
+    // best x: 1024 rows (32 words) per block
+    const dim3 grid_b(std::max(1, (n_max + 1023) / 1024), capacity);
+    eval_bestx_kernel<<<grid_b, 256, 0, st>>>(descs, 1024);
+    eval_mark_kernel<<<(capacity + 127) / 128, 128, 0, st>>>(const_cast<InstDesc *>(descs), capacity);
 }
 
 // ---------------------------------------------------------------------------

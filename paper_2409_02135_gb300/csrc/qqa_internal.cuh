@@ -387,8 +387,9 @@ void launch_dense_planes(const InstDesc *descs, int32_t slot, int32_t n, int32_t
 void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st);
 void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
-void launch_eval(const InstDesc *descs, const Tile *tiles, const int32_t *num_tiles, int32_t grid, int32_t rows_per_tile,
-                 int32_t capacity, int32_t S_max_pad, int32_t prec, cudaStream_t st);
+// rounding, exact costs, best replica: n_max the largest active n, total_rows the sum of active n
+void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
+                 int32_t prec, cudaStream_t st);
 void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
                        int32_t which, float *dst, cudaStream_t st);
 void launch_unpack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,

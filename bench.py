@@ -78,6 +78,17 @@ KERNEL_SYMBOL = {"direct": "qqa_step_kernel", "staged": "qqa_step_tiled_kernel",
                  "dense": "qqa_step_dense_kernel", "pipe": "qqa_step_pipe_kernel"}
 
 
+def read_tensor_peak():
+    """Dense fp16/bf16 tensor peak (the two have the same rate): the measured
+    cuBLAS bf16 burst figure, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (bf16 burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def kernel_source_hash(kernel: str) -> str:
     """Hash of the sources the step kernel variant is compiled from."""
     h = hashlib.sha256()
@@ -224,6 +235,31 @@ def time_to_quality(workload: str, run, count: int, anneal_start, chunk_events, 
             "instances": min(count, len(ref)), "target": "0.99 x oracle mean final best (4 seeds)"}
 
 
+def time_to_quality_plain(workload: str, runs1, job_start, chunk_end_events):
+    """The plain job anneals the instances one after another: seconds from the
+    start of the job until instance j's best feasible objective first reaches
+    99% of the oracle's mean final best (its wait for the earlier instances
+    included)."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_quality_{workload}.json")
+    if not os.path.exists(path):
+        return None
+    ref = json.load(open(path))["instances"]
+    times = []
+    for j in range(min(len(runs1), len(ref))):
+        target = ref[j]["oracle_mean_best"]
+        hist, _ = runs1[j].history(0)
+        for e, best in enumerate(hist):
+            if best > -(2 ** 62) and best >= 0.99 * target and e < len(chunk_end_events[j]):
+                times.append(job_start.elapsed_time(chunk_end_events[j][e]) / 1000.0)
+                break
+    if not times:
+        return {"reached": 0, "instances": min(len(runs1), len(ref))}
+    reached = len(times)
+    times.sort()
+    return {"median_s": times[len(times) // 2], "max_s": times[-1], "reached": reached,
+            "instances": min(len(runs1), len(ref)), "target": "0.99 x oracle mean final best (4 seeds)"}
+
+
 # ----------------------------------------------------------------- oracle leg
 def oracle_sample(wl, budget_steps: int):
     """The FP64 oracle on a bounded sample: the first instance, the first
@@ -351,10 +387,20 @@ def run_ours(args):
     peak, peak_kind = read_peak()
     achieved = alg_bytes / avg_launch_s / 1e9
     variant = ["auto", "direct", "staged", "stream", "dense", "pipe"][run.config().kernel]
+    tensor = None
+    if variant == "dense":
+        # the tensor-core step's contraction: A (n_pad^2, fp16) times two fp16 planes of width N
+        N = run.config().kernel_param
+        flops = sum(2.0 * 2.0 * float((i.graph.n + 127) // 128 * 128) ** 2 * N for i in wl.instances)
+        tpeak, tkind = read_tensor_peak()
+        tensor = {"achieved": flops / avg_launch_s / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                  "frac": flops / avg_launch_s / 1e12 / tpeak, "flops_per_launch": flops, "peak_source": tkind}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(args.workload, variant), "peak_source": peak_kind,
                 "kernel": KERNEL_SYMBOL[variant], "algorithmic_bytes_per_launch": alg_bytes,
                 "avg_launch_us": avg_launch_s * 1e6, "step_share_of_device_time": step_ms / sum(ms)}
+    if tensor is not None:
+        roofline["tensor"] = tensor
 
     # end to end through the public API with host buffers (CSR in, results out)
     e2e = None
@@ -407,19 +453,65 @@ def run_ours(args):
         torch.cuda.synchronize()
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        plain_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(chunks)] for _ in runs1]
         e0.record(stream)
-        for r1 in runs1:
+        for j, r1 in enumerate(runs1):
             r1.reset(50_000)
             for c in range(chunks):
                 r1.steps(min(R, K - c * R))
+                plain_ev[j][c].record(stream)
                 r1.eval()
         e1.record(stream)
         torch.cuda.synchronize()
+        for r1 in runs1:
+            r1.sync()   # refreshes the evaluation history the time to quality reads
         plain_s = e0.elapsed_time(e1) / 1000.0
         plain = {"value": replica_steps / plain_s, "unit": METRIC, "ms_per_step": 1000 * plain_s,
-                 "batched_over_plain": (replica_steps / (statistics.mean(ms) / 1000.0)) / (replica_steps / plain_s)}
+                 "precision": "fp32" if wl.instances[0].params.precision == W.FP32 else "bf16",
+                 "batched_over_plain": (replica_steps / (statistics.mean(ms) / 1000.0)) / (replica_steps / plain_s),
+                 "time_to_oracle_quality": time_to_quality_plain(args.workload, runs1, e0, plain_ev)}
         for r1 in runs1:
             r1.close()
+
+    # the same instances batched with BF16 storage (FP32 master and arithmetic),
+    # against the plain FP32 path above
+    bf16 = None
+    if not args.no_plain and plain is not None and wl.instances[0].params.precision == W.FP32:
+        params_b = [qqa.make_params(inst.params.with_(precision=W.BF16)) for inst in wl.instances]
+        cfg_b = qqa.LaunchConfig(use_graphs=1)
+        if args.autotune:
+            cfg_b, _ = qqa.autotune(probs, params_b, trial_steps=100, stream=stream, allocator=alloc)
+            cfg_b.use_graphs = 1
+        run_b = qqa.Run.create(probs, params_b, config=cfg_b, stream=stream, allocator=alloc)
+
+        def anneal_b(seed, ev=None):
+            run_b.reset(seed)
+            for c in range(chunks):
+                run_b.steps(min(R, K - c * R))
+                if ev is not None:
+                    ev[c][1].record(stream)
+                run_b.eval()
+
+        anneal_b(60_000)
+        torch.cuda.synchronize()
+        msb, ev_b, start_b = [], None, None
+        for k in range(3):
+            flush.zero_()
+            ev_b = [(None, torch.cuda.Event(enable_timing=True)) for _ in range(chunks)]
+            start_b = torch.cuda.Event(enable_timing=True)
+            end_b = torch.cuda.Event(enable_timing=True)
+            start_b.record(stream)
+            anneal_b(70_000 + k, ev_b)
+            end_b.record(stream)
+            torch.cuda.synchronize()
+            msb.append(start_b.elapsed_time(end_b))
+        run_b.sync()
+        value_b = replica_steps / (statistics.mean(msb) / 1000.0)
+        bf16 = {"value": value_b, "unit": METRIC, "ms_per_step": statistics.mean(msb),
+                "over_plain_fp32": value_b / plain["value"],
+                "time_to_oracle_quality": time_to_quality(args.workload, run_b, len(probs), start_b, ev_b, R),
+                "launch": ["auto", "direct", "staged", "stream", "dense", "pipe"][run_b.config().kernel]}
+        run_b.close()
 
     prec = wl.instances[0].params.precision
     line = {
@@ -440,7 +532,7 @@ def run_ours(args):
         "replica_node_updates_per_s": sum_over_ranks(sum(i.graph.n * i.params.S * i.params.steps
                                                          for i in wl.instances) * args.steps, world) / dev_s_max,
         "wall_s_timed_region": wall, "best_objective_per_instance": quality,
-        "time_to_oracle_quality": ttq, "plain": plain,
+        "time_to_oracle_quality": ttq, "plain": plain, "batched_bf16": bf16,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -602,6 +602,21 @@ static int setup_dense_slot(qqa_run *r, int32_t k, InstDesc &d, std::vector<void
     if (tm) dev.push_back(tm);
     if (!d.dense_A || !d.dense_XT || !tm) return fail(QQA_ENOMEM, "dense adjacency of %lld x %lld fp16 does not fit",
                                                      (long long)n_pad, (long long)n_pad);
+    // unit-weight graphs: adjacency and rounded replicas as bitsets, so the
+    // evaluation counts by popcount
+    d.dense_Abits = nullptr;
+    d.dense_xbits = nullptr;
+    size_t ab_bytes = 0;
+    if (!d.w) {
+        ab_bytes = (size_t)n_pad * (size_t)(n_pad / 32) * 4;
+        const size_t xb_bytes = (size_t)((r->slots[k].S_pad + 31) / 32 * 32) * (size_t)(n_pad / 32) * 4;
+        d.dense_Abits = (uint32_t *)r->alloc.get(ab_bytes, st);
+        d.dense_xbits = (uint32_t *)r->alloc.get(xb_bytes, st);
+        if (d.dense_Abits) dev.push_back(d.dense_Abits);
+        if (d.dense_xbits) dev.push_back(d.dense_xbits);
+        if (!d.dense_Abits || !d.dense_xbits) return fail(QQA_ENOMEM, "dense adjacency bitsets do not fit");
+        QQA_CK(cudaMemsetAsync(d.dense_Abits, 0, ab_bytes, st));
+    }
     d.dense_tmaps = tm;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return fail(QQA_ECUDA, "cuTensorMapEncodeTiled is not available");
@@ -623,7 +638,6 @@ static int setup_dense_slot(qqa_run *r, int32_t k, InstDesc &d, std::vector<void
     QQA_CK(cudaMemsetAsync(d.dense_XT, 0, x_bytes, st));
     QQA_CK(cudaMemcpyAsync(tm, maps, sizeof maps, cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
-    (void)k;
     return QQA_OK;
 }
 
@@ -973,8 +987,8 @@ extern "C" int qqa_run_eval(qqa_run *r, void *stream)
             n_max = std::max(n_max, s.n);
             total_rows += s.n;
         }
-    launch_eval(r->d_descs, r->capacity, n_max, total_rows, r->S_max_pad, r->prec, st);
-    g_launches += 5;
+    launch_eval(r->d_descs, r->capacity, n_max, total_rows, r->S_max_pad, r->prec, r->dense_N > 0, st);
+    g_launches += r->dense_N > 0 ? 7 : 5;
     QQA_CK_LAUNCH("eval");
     for (auto &s : r->slots)
         if (s.active && s.t != s.last_eval_t) s.last_eval_t = s.t;

@@ -170,7 +170,7 @@ __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, int32_t ro
 {
     extern __shared__ long long sh_cnt[];   // [3][S_pad32]
     const InstDesc &d = descs[blockIdx.y];
-    if (!needs_eval(d)) return;
+    if (!needs_eval(d) || d.dense_Abits) return;   // bitset slots are counted by eval_count_bits_kernel
     const int r0 = blockIdx.x * rows;
     if (r0 >= d.n) return;   // block-uniform
     const int row_end = min(r0 + rows, d.n);
@@ -217,6 +217,74 @@ __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, int32_t ro
         if (sh_cnt[s]) atomicAdd(&d.counts[s], (unsigned long long)sh_cnt[s]);
         if (sh_cnt[S32 + s]) atomicAdd(&d.counts[d.S_pad + s], (unsigned long long)sh_cnt[S32 + s]);
         if (sh_cnt[2 * S32 + s]) atomicAdd(&d.counts[2 * d.S_pad + s], (unsigned long long)sh_cnt[2 * S32 + s]);
+    }
+}
+
+// Slots with adjacency bitsets (unit-weight graphs on the tensor-core step):
+// the rounded replicas transposed to node bitsets, xbits[s][k] bit b = x_{32k+b}
+// of replica s. One warp per 32 x 32 block (32 nodes, 32 replicas): lane i
+// holds the replica word of node 32k + i, and 32 ballots transpose it.
+__global__ void eval_xbits_kernel(const InstDesc *__restrict__ descs)
+{
+    const InstDesc &d = descs[blockIdx.y];
+    if (!needs_eval(d) || !d.dense_Abits) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = d.n_pad >> 5;
+    const int blk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (blk >= nw * d.W) return;   // warp-uniform
+    const int k = blk % nw, w = blk / nw;
+    const int i = 32 * k + lane;
+    const unsigned v = i < d.n ? d.bits[(size_t)i * d.W + w] : 0u;
+    unsigned mine = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, (v >> b) & 1u);
+        if (lane == b) mine = m;
+    }
+    d.dense_xbits[(size_t)(32 * w + lane) * nw + k] = mine;
+}
+
+// Exact costs by popcount, one warp per replica s (lanes over the 32-node
+// words of a row): size = |X_s|; inside = sum over the selected nodes i of
+// |N(i) & X_s|, halved (each edge is seen from both ends); unit-weight
+// cut = sum of the selected nodes' degrees - 2 inside.
+__global__ void eval_count_bits_kernel(const InstDesc *__restrict__ descs)
+{
+    const InstDesc &d = descs[blockIdx.y];
+    if (!needs_eval(d) || !d.dense_Abits) return;
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (s >= d.S) return;   // warp-uniform
+    const int nw = d.n_pad >> 5;
+    const uint32_t *xs = d.dense_xbits + (size_t)s * nw;
+    long long size = 0, twice_inside = 0, degsum = 0;
+    for (int kb = 0; kb < nw; kb += 32) {
+        // this lane's word of X_s, then walk the selected nodes of every word of the batch
+        const unsigned mine = kb + lane < nw ? xs[kb + lane] : 0u;
+        size += __popc(mine);
+        for (int kk = 0; kk < 32 && kb + kk < nw; ++kk) {
+            unsigned sel = __shfl_sync(0xffffffffu, mine, kk);
+            while (sel) {   // warp-uniform
+                const int b = __ffs(sel) - 1;
+                sel &= sel - 1;
+                const int i = 32 * (kb + kk) + b;
+                const uint32_t *arow = d.dense_Abits + (size_t)i * nw;
+                for (int k = lane; k < nw; k += 32) twice_inside += __popc(arow[k] & xs[k]);
+                if (lane == 0) degsum += d.row_ptr[i + 1] - d.row_ptr[i];
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        size += __shfl_xor_sync(0xffffffffu, size, off);
+        twice_inside += __shfl_xor_sync(0xffffffffu, twice_inside, off);
+        degsum += __shfl_xor_sync(0xffffffffu, degsum, off);
+    }
+    if (lane == 0) {
+        const long long inside = twice_inside / 2;
+        d.counts[s] = (unsigned long long)size;
+        d.counts[d.S_pad + s] = (unsigned long long)inside;
+        d.counts[2 * d.S_pad + s] = (unsigned long long)(degsum - 2 * inside);
     }
 }
 
@@ -303,7 +371,7 @@ __global__ void eval_mark_kernel(InstDesc *__restrict__ descs, int32_t capacity)
 }
 
 void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
-                 int32_t prec, cudaStream_t st)
+                 int32_t prec, bool dense, cudaStream_t st)
 {
     // rows per counting chunk: a multiple of 8, small enough for about four
     // waves of 256-thread blocks (8 per SM) over the whole run
@@ -315,6 +383,12 @@ void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t
     eval_bits_kernel<<<grid, 256, 0, st>>>(descs, rows, prec);
     const int S32 = (S_max_pad + 31) & ~31;
     eval_count_kernel<<<grid, 256, 3 * S32 * sizeof(long long), st>>>(descs, rows);
+    if (dense) {   // unit-weight slots of the tensor-core step: costs by popcount over bitsets
+        const int nw = (n_max + 127) / 128 * 4;   // 32-node words of the largest n_pad
+        const int W = S32 / 32;
+        eval_xbits_kernel<<<dim3((nw * W + 7) / 8, capacity), 256, 0, st>>>(descs);
+        eval_count_bits_kernel<<<dim3((S32 + 7) / 8, capacity), 256, 0, st>>>(descs);
+    }
     eval_finalize_kernel<<<(capacity + 7) / 8, 256, 0, st>>>(descs, capacity);
     // best x: 1024 rows (32 words) per block
     const dim3 grid_b(std::max(1, (n_max + 1023) / 1024), capacity);

@@ -46,6 +46,8 @@ struct __align__(16) InstDesc {
     uint16_t *dense_A;           // fp16 adjacency [n_pad][n_pad], zero padded
     uint16_t *dense_XT;          // fp16 state planes [2 buffers][2 (hi, lo)][dense_N][n_pad]: p^t[j][s] at [s][j]
     const void *dense_tmaps;     // 5 TMA tensor maps: adjacency, then planes (buffer 0 hi, lo, buffer 1 hi, lo)
+    uint32_t *dense_Abits;       // unit-weight graphs: adjacency bitsets [n_pad][n_pad / 32] (bit j of row i = A_ij)
+    uint32_t *dense_xbits;       // rounded replicas as node bitsets [S rounded to 32][n_pad / 32]
     int32_t n_pad, dense_N, pad4, pad5;
     // sizes
     int32_t n, S, S_pad, W;
@@ -388,8 +390,9 @@ void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t p
 void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 // rounding, exact costs, best replica: n_max the largest active n, total_rows the sum of active n
+// dense: the run keeps the tensor-core step's adjacency bitsets (costs by popcount)
 void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
-                 int32_t prec, cudaStream_t st);
+                 int32_t prec, bool dense, cudaStream_t st);
 void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
                        int32_t which, float *dst, cudaStream_t st);
 void launch_unpack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,

@@ -362,8 +362,12 @@ __global__ void dense_adjacency_kernel(const InstDesc *__restrict__ descs, int32
     const InstDesc &d = descs[slot];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
         __half *row = reinterpret_cast<__half *>(d.dense_A) + (size_t)i * d.n_pad;
-        for (int k = d.row_ptr[i]; k < d.row_ptr[i + 1]; ++k)
-            row[d.col[k]] = __float2half_rn(d.w ? (float)d.w[k] : 1.0f);
+        uint32_t *brow = d.dense_Abits ? d.dense_Abits + (size_t)i * (d.n_pad / 32) : nullptr;
+        for (int k = d.row_ptr[i]; k < d.row_ptr[i + 1]; ++k) {
+            const int j = d.col[k];
+            row[j] = __float2half_rn(d.w ? (float)d.w[k] : 1.0f);
+            if (brow) brow[j >> 5] |= 1u << (j & 31);   // this thread owns row i
+        }
     }
 }
 

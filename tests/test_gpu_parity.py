@@ -447,6 +447,34 @@ def test_round_eval_is_exact(kind, prec):
             assert (o, f) == (want.obj[want.best], True)
 
 
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+@pytest.mark.parametrize("n,p_edge,S,weighted", [(300, 0.15, 128, False), (1100, 0.05, 100, False),
+                                                 (257, 0.3, 37, False), (200, 0.1, 64, True)])
+def test_round_eval_on_the_tensor_core_step_is_exact(kind, n, p_edge, S, weighted):
+    """Tensor-core runs of unit-weight graphs count costs by popcount over
+    adjacency and replica bitsets (weighted ones by the per-edge kernel): costs,
+    feasibility, energies and the best replica equal the oracle's evaluation of
+    the GPU state. n = 1100 spans two 32-word batches of a bitset row; 257 and
+    S = 37 leave ragged words."""
+    weighted = weighted and kind == MAXCUT
+    g = _graph(kind, n, p_edge, 60 + kind, weighted=weighted)
+    prm = Params(S=S, steps=200, seed=5, precision=FP32, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    run = make_run(kind, g, prm, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
+    assert run.config().kernel == qqa.KERNEL_DENSE
+    for k in (41, 120):
+        run.steps(k)
+        run.eval()
+        run.sync()
+        res = run.result(0)
+        X = run.get_state(0)[0].astype(np.float64)
+        want = oracle.round_eval(kind, g, np.float32(prm.lam), X)
+        np.testing.assert_array_equal(res["obj"], want.obj)
+        np.testing.assert_array_equal(res["viol"], want.viol)
+        np.testing.assert_array_equal(res["feasible"], want.feasible)
+        np.testing.assert_array_equal(res["energy"], want.energy)
+        assert res["best"] == want.best
+
+
 def test_history_and_anneal_entry_point():
     g = _graph(MIS, 100, 0.05, 0)
     p = Params(S=8, steps=1000, round_every=50, seed=0)

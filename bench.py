@@ -34,6 +34,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+from qqa_inputs import graphs as G  # noqa: E402
 from qqa_inputs import workloads as W  # noqa: E402
 
 METRIC = "replica-steps/s"
@@ -51,6 +52,12 @@ def build_workload(name: str, rank: int):
         return W.maxcut_large(family="ba4", seed=7 + rank)
     if name == "mis_cliqueblocks512":
         return W.batched_mis(base_seed=5000 + 512 * rank)
+    m = re.fullmatch(r"mis_rrg_d(\d+)_n(\d+)(?:_x(\d+))?(?:_K(\d+))?", name)
+    if m:   # e.g. mis_rrg_d20_n100000 (5 graphs, 3000 steps), mis_rrg_d20_n1000000_x1_K3000
+        d, n = int(m.group(1)), int(m.group(2))
+        num = int(m.group(3)) if m.group(3) else 5
+        steps = int(m.group(4)) if m.group(4) else 3000
+        return W.rrg_mis(n=n, d=d, steps=steps, num_graphs=num, base_seed=3000 + num * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -532,6 +539,8 @@ def run_ours(args):
         "replica_node_updates_per_s": sum_over_ranks(sum(i.graph.n * i.params.S * i.params.steps
                                                          for i in wl.instances) * args.steps, world) / dev_s_max,
         "wall_s_timed_region": wall, "best_objective_per_instance": quality,
+        "objective_density_per_instance": [q / i.graph.n if q is not None and q > -(2 ** 62) else None
+                                           for q, i in zip(quality, wl.instances)],
         "time_to_oracle_quality": ttq, "plain": plain, "batched_bf16": bf16,
     }
     if rank == 0:
@@ -610,6 +619,51 @@ def run_serving(args):
     return 0
 
 
+# ------------------------------------------------------------------ ablations
+def run_ablation(args):
+    """The paper's ablation sweeps (Sec. 6, Fig. 4), which it reports only as
+    curves: independent-set size on MIS against (schedule) the number of steps
+    with gamma_0 = -2 on an ER graph shaped like the largest ER instances
+    (n = 10,000, p = 0.02), (gamma0) the initial gamma at a fixed schedule on
+    the same graph, and (alpha) the communication strength with S = 512 on an
+    ER-[700-800]-shaped graph. Five seeds per point, all seeds of a point in one
+    batched launch; one JSON line per point (mean and population std of the
+    best feasible objective, and the anneal time)."""
+    import torch
+    import paper_2409_02135_gb300 as qqa
+    if args.ablation in ("schedule", "gamma0"):
+        g = G.erdos_renyi(10_000, 0.02, 4242)
+        S = 32
+        if args.ablation == "schedule":
+            points = [{"steps": k, "gamma_min": -2.0} for k in (100, 300, 1000, 3000, 10000)]
+        else:
+            points = [{"steps": 3000, "gamma_min": g0} for g0 in (-8.0, -4.0, -2.0, -1.0, -0.5, 0.0, 0.1)]
+    else:
+        g = G.erdos_renyi(750, 0.15, 1000)
+        S = 512
+        points = [{"steps": 3000, "gamma_min": -2.0, "alpha_comm": a} for a in (0.0, 0.03, 0.1, 0.3, 1.0)]
+    stream = torch.cuda.current_stream()
+    for pt in points:
+        ps = [W.Params(S=S, seed=seed, lr=W.RECIPE_LR, **pt) for seed in range(5)]
+        probs = [qqa.Problem(W.MIS, g, stream=stream) for _ in ps]
+        cps = [qqa.make_params(p) for p in ps]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run = qqa.anneal(probs, cps, stream=stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = []
+        for k in range(len(ps)):
+            r = run.result(k, with_x=False)
+            best.append(int(r["obj"][r["best"]]) if r["best"] >= 0 else 0)
+        run.close()
+        line = {"ablation": args.ablation, "graph": {"n": g.n, "nnz": g.nnz}, "S": S, **pt, "seeds": len(ps),
+                "best_mean": statistics.mean(best), "best_std": statistics.pstdev(best), "best": best,
+                "anneal_s": dt}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -617,8 +671,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mis_er700_800",
-                    choices=["mis_er700_800", "mis_er100", "maxcut_regular3", "maxcut_ba4", "mis_cliqueblocks512",
-                             "serving"])
+                    help="mis_er700_800 (default), mis_er100, maxcut_regular3, maxcut_ba4, mis_cliqueblocks512, "
+                         "serving, or mis_rrg_d<d>_n<n>[_x<graphs>][_K<steps>] (S = 1 random regular graphs)")
     ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense", "pipe"], default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
@@ -634,7 +688,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--ablation", choices=["schedule", "gamma0", "alpha"], default=None,
+                    help="run one of the paper's ablation sweeps instead of the benchmark")
     args = ap.parse_args()
+    if args.ablation:
+        return run_ablation(args)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -103,6 +103,21 @@ def er_mis_paper(num_graphs: int = 16, S: int = 128, steps: int = 3000, base_see
                     f"MIS, {num_graphs} ER graphs n~U[700,800], p=0.15, S={S}, {steps} steps")
 
 
+def rrg_mis(n: int = 100_000, d: int = 20, steps: int = 3000, num_graphs: int = 5, base_seed: int = 3000,
+            run_seed: int = 0, precision: int = FP32) -> Workload:
+    """MIS on random d-regular graphs with a single replica (S = 1), the setting of
+    the paper's RRG study (Sec. 5.1, regular random graphs: d = 20 and 100, n from
+    1e4 to 1e6, five graphs, 3000 or 30000 steps). The quality measure is the
+    independence density |IS| / n."""
+    insts = []
+    for k in range(num_graphs):
+        g = G.random_regular(n, d, base_seed + k)
+        insts.append(Instance(MIS, g, Params(S=1, steps=steps, seed=run_seed + k, precision=precision, lr=RECIPE_LR),
+                              f"rrg{d}_{n}_{k}"))
+    return Workload(f"mis_rrg_d{d}_n{n}_x{num_graphs}_S1_K{steps}", insts,
+                    f"{num_graphs} MIS random {d}-regular graphs, n={n}, S=1, {steps} steps")
+
+
 def maxcut_large(n: int = 100_000, S: int = 256, steps: int = 5000, family: str = "regular3",
                  seed: int = 7, run_seed: int = 0, precision: int = BF16) -> Workload:
     """Max-cut on a random 3-regular or Barabasi-Albert (m=4) graph with unit

@@ -528,3 +528,23 @@ def test_batched_bf16_quality_matches_oracle(kind, gen, S, steps):
         o = oracle.anneal(kind, g, as_f32(p.with_(precision=FP32)))
         cpu.append(o.eval.obj[o.eval.best])
     assert abs(np.mean(gpu) - np.mean(cpu)) <= 0.01 * np.mean(cpu)
+
+
+def test_rrg_single_replica_quality_matches_oracle():
+    """MIS on a random 20-regular graph with one replica (S = 1, the paper's RRG
+    setting; the communication term vanishes): 16 seeds batched in one launch,
+    mean independence density within 1% of the oracle's on the same seeds, every
+    result feasible."""
+    g = G.random_regular(2000, 20, 11)
+    ps = [Params(S=1, steps=3000, seed=seed, lr=1.0) for seed in range(16)]
+    run = qqa.anneal([qqa.Problem(MIS, g) for _ in ps], [qqa.make_params(p) for p in ps])
+    gpu, cpu = [], []
+    for k, p in enumerate(ps):
+        r = run.result(k)
+        assert r["best"] == 0 and r["feasible"][0]
+        gpu.append(r["obj"][0] / g.n)
+        o = oracle.anneal(MIS, g, as_f32(p))
+        assert o.eval.best == 0
+        cpu.append(o.eval.obj[0] / g.n)
+    assert abs(np.mean(gpu) - np.mean(cpu)) <= 0.01 * np.mean(cpu)
+    assert 0.15 < np.mean(gpu) < 0.25   # near the independence ratio of random 20-regular graphs

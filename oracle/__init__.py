@@ -83,6 +83,15 @@ def _load():
             "oracle_round_eval": (i32, [i32, i32, I32, I32, I32, dbl, i32, D, I64, I64, U8, D]),
             "oracle_anneal": (i32, [P, i32, I32, I32, I32, i32, i32, I64, I64, U8, D, I32, I64, i32, D]),
             "oracle_num_threads": (i32, []),
+            "oracle_color_entropy": (dbl, [i32, i32, D, i32]),
+            "oracle_color_relaxed_conflicts": (dbl, [i32, i32, I32, I32, D]),
+            "oracle_color_conflicts": (ctypes.c_int64, [i32, I32, I32, I32]),
+            "oracle_color_objective": (dbl, [P, i32, i32, I32, I32, dbl, D]),
+            "oracle_color_gradient": (None, [P, i32, i32, I32, I32, dbl, D, D, D]),
+            "oracle_color_step": (None, [P, i32, i32, I32, I32, i32, D, D, D, D, D]),
+            "oracle_color_init": (None, [i32, i32, i32, u64, D]),
+            "oracle_color_round": (i32, [i32, i32, i32, I32, I32, D, I32, I64]),
+            "oracle_color_anneal": (i32, [P, i32, i32, I32, I32, i32, I64, I32, D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -285,3 +294,109 @@ def anneal(kind: int, graph, p, steps: int | None = None, round_every: int | Non
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+# ---------------------------------------------------------------------------
+# Categorical PQQA for graph colouring (App. B, App. C.4). W has shape
+# [n, K, S] (node, colour, replica); sigma arrays passed to the entropy and
+# relaxed-conflict functions have shape [n, K] (one replica).
+# ---------------------------------------------------------------------------
+COLORING = 3
+
+
+def color_entropy(sig, a_ent: int) -> float:
+    sg = np.ascontiguousarray(sig, dtype=np.float64)
+    n, K = sg.shape
+    return float(_load().oracle_color_entropy(n, K, _ptr(sg, ctypes.c_double), a_ent))
+
+
+def color_relaxed_conflicts(graph, sig) -> float:
+    rp, col, _ = _graph_arrays(graph)
+    sg = np.ascontiguousarray(sig, dtype=np.float64)
+    return float(_load().oracle_color_relaxed_conflicts(graph.n, sg.shape[1], _ptr(rp, ctypes.c_int32),
+                                                        _ptr(col, ctypes.c_int32), _ptr(sg, ctypes.c_double)))
+
+
+def color_conflicts(graph, x) -> int:
+    rp, col, _ = _graph_arrays(graph)
+    xx = np.ascontiguousarray(x, dtype=np.int32)
+    return int(_load().oracle_color_conflicts(graph.n, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                              _ptr(xx, ctypes.c_int32)))
+
+
+def color_sigma(W) -> np.ndarray:
+    """Clamp-normalise over the colour axis of W[n, K, S] (plain numpy, for tests)."""
+    Wc = np.clip(np.asarray(W, dtype=np.float64), 0.0, 1.0)
+    tot = Wc.sum(axis=1, keepdims=True)
+    K = Wc.shape[1]
+    return np.where(tot > 0, Wc / np.where(tot > 0, tot, 1.0), 1.0 / K)
+
+
+def color_objective(graph, K: int, p, gamma_value: float, W) -> float:
+    rp, col, _ = _graph_arrays(graph)
+    Wc = np.ascontiguousarray(W, dtype=np.float64)
+    assert Wc.shape == (graph.n, K, p.S)
+    pp = _params(COLORING, p)
+    return float(_load().oracle_color_objective(ctypes.byref(pp), graph.n, K, _ptr(rp, ctypes.c_int32),
+                                                _ptr(col, ctypes.c_int32), gamma_value, _ptr(Wc, ctypes.c_double)))
+
+
+def color_gradient(graph, K: int, p, gamma_value: float, W, with_scale: bool = False):
+    rp, col, _ = _graph_arrays(graph)
+    Wc = np.ascontiguousarray(W, dtype=np.float64)
+    assert Wc.shape == (graph.n, K, p.S)
+    G = np.zeros_like(Wc)
+    Gs = np.zeros_like(Wc)
+    pp = _params(COLORING, p)
+    _load().oracle_color_gradient(ctypes.byref(pp), graph.n, K, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                  gamma_value, _ptr(Wc, ctypes.c_double), _ptr(G, ctypes.c_double),
+                                  _ptr(Gs, ctypes.c_double))
+    return (G, Gs) if with_scale else G
+
+
+def color_step(graph, K: int, p, t: int, W, m, v) -> StepOut:
+    """One annealing step t of the colouring state (W, m, v) [n, K, S]; inputs are not modified."""
+    rp, col, _ = _graph_arrays(graph)
+    Wn = np.array(W, dtype=np.float64, copy=True)
+    mm = np.array(m, dtype=np.float64, copy=True)
+    vv = np.array(v, dtype=np.float64, copy=True)
+    assert Wn.shape == (graph.n, K, p.S) == mm.shape == vv.shape
+    G = np.zeros_like(Wn)
+    Gs = np.zeros_like(Wn)
+    pp = _params(COLORING, p)
+    _load().oracle_color_step(ctypes.byref(pp), graph.n, K, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32), t,
+                              _ptr(Wn, ctypes.c_double), _ptr(mm, ctypes.c_double), _ptr(vv, ctypes.c_double),
+                              _ptr(G, ctypes.c_double), _ptr(Gs, ctypes.c_double))
+    return StepOut(Wn, mm, vv, G, Gs)
+
+
+def color_init(n: int, K: int, S: int, seed: int) -> np.ndarray:
+    W = np.zeros((n, K, S), dtype=np.float64)
+    _load().oracle_color_init(n, K, S, seed, _ptr(W, ctypes.c_double))
+    return W
+
+
+def color_round(graph, K: int, W):
+    """(x [n, S] colours, conflicts [S], best replica) of the rounding argmax_k sigma."""
+    rp, col, _ = _graph_arrays(graph)
+    Wc = np.ascontiguousarray(W, dtype=np.float64)
+    S = Wc.shape[2]
+    x = np.zeros((graph.n, S), dtype=np.int32)
+    conf = np.zeros(S, dtype=np.int64)
+    best = _load().oracle_color_round(graph.n, K, S, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                      _ptr(Wc, ctypes.c_double), _ptr(x, ctypes.c_int32), _ptr(conf, ctypes.c_int64))
+    return x, conf, int(best)
+
+
+def color_anneal(graph, K: int, p, steps: int | None = None):
+    """Init + steps (default p.steps) + rounding: (conflicts [S], best replica, x [n, S], W [n, K, S])."""
+    rp, col, _ = _graph_arrays(graph)
+    S = p.S
+    conf = np.zeros(S, dtype=np.int64)
+    x = np.zeros((graph.n, S), dtype=np.int32)
+    W = np.zeros((graph.n, K, S), dtype=np.float64)
+    pp = _params(COLORING, p)
+    best = _load().oracle_color_anneal(ctypes.byref(pp), graph.n, K, _ptr(rp, ctypes.c_int32),
+                                       _ptr(col, ctypes.c_int32), -1 if steps is None else steps,
+                                       _ptr(conf, ctypes.c_int64), _ptr(x, ctypes.c_int32), _ptr(W, ctypes.c_double))
+    return conf, int(best), x, W

@@ -447,6 +447,270 @@ int32_t oracle_anneal(const oracle_params *P, int32_t n, const int32_t *rp, cons
     return nh;
 }
 
+/* ================================================================== */
+/* Categorical PQQA for graph colouring (App. B; Clamp-normalise of     */
+/* App. C.4; the colouring energy of App. D.1 with the sign that       */
+/* minimises conflicts).                                                */
+/*                                                                      */
+/* State W[i][k][s] in [0,1] (node i, colour k, replica s), flattened   */
+/* as ((i * K + k) * S + s). sigma_ik = W_ik / sum_k' W_ik' (the clamp  */
+/* is the identity on [0,1]; a row of zeros maps to 1/K).               */
+/* Readings where the paper is silent (also listed in the design doc):       */
+/*   - after each update W is projected to [0,1], as p is in the binary */
+/*     method; sigma is re-formed from the projected W;                 */
+/*   - the communication term acts on sigma, per (node, colour), over   */
+/*     the S replicas;                                                  */
+/*   - random numbers use the binary counters with row index i*K + k;   */
+/*   - rounding: x_i = argmax_k sigma_ik, ties to the lowest colour.    */
+/* ================================================================== */
+
+/* c_K of the categorical alpha-entropy (App. B): 1 / ((K-1)((K-1)^(a-1) + 1)) */
+static double color_cK(int32_t K, int32_t a)
+{
+    return 1.0 / ((double)(K - 1) * (ipow((double)(K - 1), a - 1) + 1.0));
+}
+
+/* sigma of row (i, s): out[k] for k < K; returns the row sum of W (0: uniform) */
+static double color_sigma_row(const double *W, int32_t K, int32_t S, int32_t i, int32_t s, double *out)
+{
+    double sum = 0.0;
+    for (int32_t k = 0; k < K; ++k) sum += W[((int64_t)i * K + k) * S + s];
+    for (int32_t k = 0; k < K; ++k) out[k] = sum > 0.0 ? W[((int64_t)i * K + k) * S + s] / sum : 1.0 / (double)K;
+    return sum;
+}
+
+/* s_K(sigma) = sum_i { 1 - c_K sum_k (K sigma_ik - 1)^a }, sigma[n][K] */
+double oracle_color_entropy(int32_t n, int32_t K, const double *sig, int32_t a)
+{
+    double cK = color_cK(K, a), acc = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        double inner = 0.0;
+        for (int32_t k = 0; k < K; ++k) inner += ipow((double)K * sig[(int64_t)i * K + k] - 1.0, a);
+        acc += 1.0 - cK * inner;
+    }
+    return acc;
+}
+
+/* relaxed conflicts: sum over edges {i, j} (each once) of sum_k sigma_ik sigma_jk, sigma[n][K] */
+double oracle_color_relaxed_conflicts(int32_t n, int32_t K, const int32_t *rp, const int32_t *col, const double *sig)
+{
+    double acc = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int32_t j = col[e];
+            if (j <= i) continue;
+            for (int32_t k = 0; k < K; ++k) acc += sig[(int64_t)i * K + k] * sig[(int64_t)j * K + k];
+        }
+    return acc;
+}
+
+/* conflicts of a colouring x[n]: edges {i, j} with x_i = x_j */
+int64_t oracle_color_conflicts(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *x)
+{
+    int64_t c = 0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+            if (col[e] > i && x[col[e]] == x[i]) ++c;
+    return c;
+}
+
+/* population mean and STD_eps of sigma_ik over the replicas (Eq. 10) */
+static void color_stats(const double *SIG, int32_t K, int32_t S, int32_t i, int32_t k, double comm_eps, double *mean,
+                        double *std)
+{
+    double acc = 0.0;
+    for (int32_t s = 0; s < S; ++s) acc += SIG[((int64_t)i * K + k) * S + s];
+    double m = acc / (double)S, var = 0.0;
+    for (int32_t s = 0; s < S; ++s) {
+        double d = SIG[((int64_t)i * K + k) * S + s] - m;
+        var += d * d;
+    }
+    *mean = m;
+    *std = sqrt(var / (double)S + comm_eps);
+}
+
+/* sigma of every (i, k, s) from W, same layout */
+static void color_sigma_all(int32_t n, int32_t K, int32_t S, const double *W, double *SIG)
+{
+    double *row = (double *)malloc(sizeof(double) * (size_t)K);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t s = 0; s < S; ++s) {
+            color_sigma_row(W, K, S, i, s, row);
+            for (int32_t k = 0; k < K; ++k) SIG[((int64_t)i * K + k) * S + s] = row[k];
+        }
+    free(row);
+}
+
+/*
+ * R(W) = sum_s [ conflicts^(sigma_s) + gamma s_K(sigma_s) ] - S alpha sum_{i,k} STD_ik,
+ * sigma = Clamp-normalise(W) (App. B, App. C.4, Eq. 10).
+ */
+double oracle_color_objective(const oracle_params *P, int32_t n, int32_t K, const int32_t *rp, const int32_t *col,
+                              double gamma, const double *W)
+{
+    int32_t S = P->S;
+    size_t NKS = (size_t)n * (size_t)K * (size_t)S;
+    double *SIG = (double *)malloc(sizeof(double) * (NKS ? NKS : 1));
+    double *col_sig = (double *)malloc(sizeof(double) * ((size_t)n * K ? (size_t)n * K : 1));
+    color_sigma_all(n, K, S, W, SIG);
+    double total = 0.0;
+    for (int32_t s = 0; s < S; ++s) {
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = 0; k < K; ++k) col_sig[(int64_t)i * K + k] = SIG[((int64_t)i * K + k) * S + s];
+        total += oracle_color_relaxed_conflicts(n, K, rp, col, col_sig) + gamma * oracle_color_entropy(n, K, col_sig, P->a_ent);
+    }
+    if (P->alpha_comm != 0.0)
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = 0; k < K; ++k) {
+                double mean, std;
+                color_stats(SIG, K, S, i, k, P->comm_eps, &mean, &std);
+                total -= (double)S * P->alpha_comm * std;
+            }
+    free(SIG);
+    free(col_sig);
+    return total;
+}
+
+/*
+ * dR/dW at W (interior of [0,1]): with g_ik = dR/dsigma_ik =
+ *   sum_{j in N(i)} sigma_jk                        (relaxed conflicts)
+ *   + gamma (-c_K a K (K sigma_ik - 1)^(a-1))       (entropy)
+ *   - alpha (sigma_ik - mean_ik) / STD_ik            (communication, per replica)
+ * the Clamp-normalise Jacobian d sigma_ik' / d W_ik = (delta_kk' - sigma_ik') / sum_k W
+ * gives dR/dW_ik = (g_ik - sum_k' sigma_ik' g_ik') / sum_k W (0 for a zero row).
+ * G and Gs (sum of absolute contributions, same propagation) are [n][K][S].
+ */
+void oracle_color_gradient(const oracle_params *P, int32_t n, int32_t K, const int32_t *rp, const int32_t *col,
+                           double gamma, const double *W, double *G, double *Gs)
+{
+    int32_t S = P->S;
+    size_t NKS = (size_t)n * (size_t)K * (size_t)S;
+    double *SIG = (double *)malloc(sizeof(double) * (NKS ? NKS : 1));
+    color_sigma_all(n, K, S, W, SIG);
+    double cK = color_cK(K, P->a_ent);
+    #pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < n; ++i) {
+        double *gs = (double *)malloc(sizeof(double) * (size_t)K);
+        double *as = (double *)malloc(sizeof(double) * (size_t)K);
+        double *mean = (double *)malloc(sizeof(double) * (size_t)K);
+        double *std = (double *)malloc(sizeof(double) * (size_t)K);
+        for (int32_t k = 0; k < K; ++k) color_stats(SIG, K, S, i, k, P->comm_eps, &mean[k], &std[k]);
+        for (int32_t s = 0; s < S; ++s) {
+            double wsum = 0.0;
+            for (int32_t k = 0; k < K; ++k) wsum += W[((int64_t)i * K + k) * S + s];
+            double dot = 0.0, adot = 0.0;
+            for (int32_t k = 0; k < K; ++k) {
+                double sig = SIG[((int64_t)i * K + k) * S + s];
+                double y = 0.0;
+                for (int32_t e = rp[i]; e < rp[i + 1]; ++e) y += SIG[((int64_t)col[e] * K + k) * S + s];
+                double ent = gamma * (-cK * (double)P->a_ent * (double)K * ipow((double)K * sig - 1.0, P->a_ent - 1));
+                double comm = P->alpha_comm != 0.0 ? -P->alpha_comm * (sig - mean[k]) / std[k] : 0.0;
+                gs[k] = y + ent + comm;
+                as[k] = fabs(y) + fabs(ent) + fabs(comm);
+                dot += sig * gs[k];
+                adot += sig * as[k];
+            }
+            for (int32_t k = 0; k < K; ++k) {
+                int64_t e = ((int64_t)i * K + k) * S + s;
+                G[e] = wsum > 0.0 ? (gs[k] - dot) / wsum : 0.0;
+                if (Gs) Gs[e] = wsum > 0.0 ? (as[k] + adot) / wsum : 0.0;
+            }
+        }
+        free(gs); free(as); free(mean); free(std);
+    }
+    free(SIG);
+}
+
+/*
+ * One step on W[n][K][S] (in place), as the binary step: AdamW with decoupled
+ * decay, + sqrt(2 lr T) xi with xi the Gaussian of counter row i*K + k, then
+ * the projection to [0,1]. grad/gabs (optional) receive dR/dW and its scale.
+ */
+void oracle_color_step(const oracle_params *P, int32_t n, int32_t K, const int32_t *rp, const int32_t *col, int32_t t,
+                       double *W, double *m, double *v, double *grad, double *gabs)
+{
+    int32_t S = P->S;
+    size_t NKS = (size_t)n * (size_t)K * (size_t)S;
+    double *G = (double *)malloc(sizeof(double) * (NKS ? NKS : 1));
+    double *Gs = (double *)malloc(sizeof(double) * (NKS ? NKS : 1));
+    oracle_color_gradient(P, n, K, rp, col, oracle_gamma(P, t), W, G, Gs);
+    double bc1 = 1.0 - pow(P->beta1, (double)(t + 1));
+    double bc2 = 1.0 - pow(P->beta2, (double)(t + 1));
+    double noise_scale = sqrt(2.0 * P->lr * P->temperature);
+    #pragma omp parallel for schedule(static)
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = 0; k < K; ++k)
+            for (int32_t s = 0; s < S; ++s) {
+                int64_t e = ((int64_t)i * K + k) * S + s;
+                double g = G[e];
+                double wn = W[e] * (1.0 - P->lr * P->weight_decay);
+                double mm = P->beta1 * m[e] + (1.0 - P->beta1) * g;
+                double vv = P->beta2 * v[e] + (1.0 - P->beta2) * g * g;
+                wn -= (P->lr / bc1) * mm / (sqrt(vv) / sqrt(bc2) + P->adam_eps);
+                if (noise_scale != 0.0) wn += noise_scale * oracle_gaussian(P->seed, i * K + k, s, t);
+                if (wn < 0.0) wn = 0.0;
+                if (wn > 1.0) wn = 1.0;
+                W[e] = wn;
+                m[e] = mm;
+                v[e] = vv;
+                if (grad) grad[e] = g;
+                if (gabs) gabs[e] = Gs[e];
+            }
+    free(G);
+    free(Gs);
+}
+
+/* initial W: U(0,1] of counter row i*K + k (tag 0) */
+void oracle_color_init(int32_t n, int32_t K, int32_t S, uint64_t seed, double *W)
+{
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = 0; k < K; ++k)
+            for (int32_t s = 0; s < S; ++s) W[((int64_t)i * K + k) * S + s] = oracle_uniform(seed, i * K + k, s, 0, 0);
+}
+
+/* rounding x_is = argmax_k sigma_iks (ties -> lowest k) and the conflicts of every
+ * replica; returns the replica with the fewest conflicts (ties -> lowest s) */
+int32_t oracle_color_round(int32_t n, int32_t K, int32_t S, const int32_t *rp, const int32_t *col, const double *W,
+                           int32_t *x_all, int64_t *conflicts)
+{
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    double *row = (double *)malloc(sizeof(double) * (size_t)K);
+    int32_t best = -1;
+    for (int32_t s = 0; s < S; ++s) {
+        for (int32_t i = 0; i < n; ++i) {
+            color_sigma_row(W, K, S, i, s, row);
+            int32_t arg = 0;
+            for (int32_t k = 1; k < K; ++k)
+                if (row[k] > row[arg]) arg = k;
+            x[i] = arg;
+            if (x_all) x_all[(int64_t)i * S + s] = arg;
+        }
+        conflicts[s] = oracle_color_conflicts(n, rp, col, x);
+        if (best < 0 || conflicts[s] < conflicts[best]) best = s;
+    }
+    free(x);
+    free(row);
+    return best;
+}
+
+/* full run: init, P->K steps, final rounding; W_out (optional) gets the final state */
+int32_t oracle_color_anneal(const oracle_params *P, int32_t n, int32_t K, const int32_t *rp, const int32_t *col,
+                            int32_t steps_to_run, int64_t *conflicts, int32_t *x_all, double *W_out)
+{
+    int32_t S = P->S;
+    size_t NKS = (size_t)n * (size_t)K * (size_t)S;
+    double *W = (double *)malloc(sizeof(double) * (NKS ? NKS : 1));
+    double *m = (double *)calloc(NKS ? NKS : 1, sizeof(double));
+    double *v = (double *)calloc(NKS ? NKS : 1, sizeof(double));
+    oracle_color_init(n, K, S, P->seed, W);
+    int32_t steps = steps_to_run >= 0 ? steps_to_run : P->K;
+    for (int32_t t = 0; t < steps; ++t) oracle_color_step(P, n, K, rp, col, t, W, m, v, NULL, NULL);
+    int32_t best = oracle_color_round(n, K, S, rp, col, W, x_all, conflicts);
+    if (W_out) memcpy(W_out, W, sizeof(double) * NKS);
+    free(W); free(m); free(v);
+    return best;
+}
+
 int32_t oracle_num_threads(void)
 {
 #ifdef _OPENMP

@@ -264,3 +264,42 @@ def disjoint_union(graphs) -> CSRGraph:
         off += g.n
     return from_edges(off, np.concatenate(us), np.concatenate(vs),
                       np.concatenate(ws) if weighted else None)
+
+
+def queens(rows: int, cols: int) -> CSRGraph:
+    """Queens graph of a rows x cols board: one node per square (row-major), two
+    squares adjacent when they share a row, a column or a diagonal (the COLOR
+    benchmark family queen<r>_<c>)."""
+    us, vs = [], []
+    for a in range(rows * cols):
+        ra, ca = divmod(a, cols)
+        for b in range(a + 1, rows * cols):
+            rb, cb = divmod(b, cols)
+            if ra == rb or ca == cb or abs(ra - rb) == abs(ca - cb):
+                us.append(a)
+                vs.append(b)
+    return from_edges(rows * cols, np.array(us, dtype=np.int64), np.array(vs, dtype=np.int64))
+
+
+def mycielski(level: int) -> CSRGraph:
+    """Mycielski graph of the COLOR family myciel<level>: the 5-cycle is
+    myciel2, and each level applies the Mycielski construction (nodes v_i of G,
+    copies u_i adjacent to the neighbours of v_i, and one node w adjacent to every
+    u_i), which keeps the graph triangle-free and raises the chromatic number by one
+    (myciel<l> has chromatic number l + 1)."""
+    if level < 2:
+        raise ValueError("level >= 2 (myciel2 is the 5-cycle)")
+    n = 5
+    edges = [(i, (i + 1) % 5) for i in range(5)]
+    for _ in range(level - 2):
+        new = list(edges)
+        for (a, b) in edges:          # u_a ~ v_b and u_b ~ v_a
+            new.append((n + a, b))
+            new.append((n + b, a))
+        w = 2 * n
+        for i in range(n):
+            new.append((n + i, w))
+        edges, n = new, 2 * n + 1
+    u = np.array([min(a, b) for a, b in edges], dtype=np.int64)
+    v = np.array([max(a, b) for a, b in edges], dtype=np.int64)
+    return from_edges(n, u, v)

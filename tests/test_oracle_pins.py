@@ -371,3 +371,167 @@ def test_periodic_history_is_monotone_prefix(oracle_lib):
     assert len(full.history) == 8 and len(half.history) == 4
     np.testing.assert_array_equal(full.history[:3], half.history[:3])
     assert full.history[-1] == full.eval.obj[full.eval.best]
+
+
+# ------------------------------------------- categorical colouring (NEXT) ---
+def _color_graphs():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_color_graphs.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, gen, nodes, edges, colours, conflicts = line.split()
+                rows.append((name, gen, int(nodes), int(edges), int(colours), int(conflicts)))
+    return rows
+
+
+def _make_color_graph(gen):
+    parts = gen.split(":")
+    return G.mycielski(int(parts[1])) if parts[0] == "mycielski" else G.queens(int(parts[1]), int(parts[2]))
+
+
+def test_color_graph_generators_match_the_papers_table():
+    """Queens and Mycielski graphs built from their definitions have the node and
+    edge counts of the paper's Table 9."""
+    for name, gen, nodes, edges, _, _ in _color_graphs():
+        g = _make_color_graph(gen)
+        assert (g.n, g.nnz // 2) == (nodes, edges), name
+
+
+@pytest.mark.parametrize("a", [2, 4, 6])
+def test_categorical_entropy_reduces_to_the_binary_one_at_K2(oracle_lib, a):
+    """Proposition of App. B: s_2(sigma) with sigma_i = (p_i, 1 - p_i) equals the
+    alpha-entropy s(p) of Eq. 7."""
+    rng = np.random.default_rng(a)
+    p = rng.random(40)
+    sig = np.stack([p, 1 - p], axis=1)
+    assert oracle.color_entropy(sig, a) == pytest.approx(oracle.entropy(p, a), rel=1e-14, abs=1e-12)
+
+
+@pytest.mark.parametrize("K,a", [(3, 2), (5, 4), (7, 4)])
+def test_categorical_entropy_closed_forms(oracle_lib, K, a):
+    """s_K is 0 at every one-hot row (App. B: the minimisers are the discrete
+    points), N at the uniform row 1/K (its maximum), and invariant under a
+    permutation of the colours."""
+    rng = np.random.default_rng(K)
+    n = 25
+    one_hot = np.eye(K)[rng.integers(0, K, size=n)]
+    assert oracle.color_entropy(one_hot, a) == pytest.approx(0.0, abs=1e-12)
+    assert oracle.color_entropy(np.full((n, K), 1.0 / K), a) == pytest.approx(n, rel=1e-14)
+    sig = rng.random((n, K))
+    sig /= sig.sum(axis=1, keepdims=True)
+    perm = rng.permutation(K)
+    assert oracle.color_entropy(sig[:, perm], a) == pytest.approx(oracle.color_entropy(sig, a), rel=1e-13)
+    assert oracle.color_entropy(sig, a) < n
+
+
+def test_relaxed_conflicts_equal_discrete_conflicts_on_one_hot_points(oracle_lib):
+    """At one-hot sigma the relaxed energy equals the number of conflicting
+    edges, and both equal a count over the dense adjacency matrix."""
+    g = G.erdos_renyi(30, 0.25, 8)
+    A = np.zeros((g.n, g.n), dtype=np.int64)
+    for i in range(g.n):
+        A[i, g.col[g.row_ptr[i]:g.row_ptr[i + 1]]] = 1
+    rng = np.random.default_rng(2)
+    for K in (2, 3, 6):
+        for _ in range(5):
+            x = rng.integers(0, K, size=g.n)
+            same = (x[:, None] == x[None, :]).astype(np.int64)
+            want = int(np.sum(np.triu(A * same, 1)))
+            assert oracle.color_conflicts(g, x) == want
+            assert oracle.color_relaxed_conflicts(g, np.eye(K)[x]) == pytest.approx(want, abs=1e-12)
+
+
+@pytest.mark.parametrize("K", [3, 5])
+@pytest.mark.parametrize("a_ent", [2, 4])
+@pytest.mark.parametrize("alpha", [0.0, 0.7])
+def test_color_gradient_matches_finite_differences(oracle_lib, K, a_ent, alpha):
+    """dR/dW through the Clamp-normalise map (App. C.4) equals central finite
+    differences of R (conflicts + gamma s_K - S alpha sum STD) to 1e-7 relative."""
+    g = G.erdos_renyi(9, 0.4, 30 + K)
+    p = Params(S=4, a_ent=a_ent, alpha_comm=alpha, comm_eps=1e-8)
+    rng = np.random.default_rng(K * 10 + a_ent)
+    W = 0.1 + 0.8 * rng.random((g.n, K, p.S))
+    gam = -0.8
+    Gm = oracle.color_gradient(g, K, p, gam, W)
+    h = 1e-5
+    worst = 0.0
+    for idx in np.ndindex(W.shape):
+        Wp = W.copy(); Wp[idx] += h
+        Wm = W.copy(); Wm[idx] -= h
+        fd = (oracle.color_objective(g, K, p, gam, Wp) - oracle.color_objective(g, K, p, gam, Wm)) / (2 * h)
+        worst = max(worst, abs(fd - Gm[idx]) / max(1.0, abs(Gm[idx])))
+    assert worst < 1e-7
+
+
+def test_color_step_is_torch_adamw_and_noise_then_projection(oracle_lib):
+    """A colouring step is torch.optim.AdamW (FP64) on the oracle's dR/dW, plus
+    sqrt(2 lr T) xi with xi the Gaussian of counter row i*K + k, then the
+    projection of W to [0, 1]."""
+    torch = pytest.importorskip("torch")
+    g = G.erdos_renyi(12, 0.3, 4)
+    K = 4
+    p = Params(S=5, steps=40, lr=2e-3, temperature=0.0, alpha_comm=0.3, weight_decay=0.01, seed=9)
+    rng = np.random.default_rng(3)
+    W = 0.3 + 0.4 * rng.random((g.n, K, p.S))
+    wt = torch.tensor(W, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.AdamW([wt], lr=p.lr, betas=(p.beta1, p.beta2), eps=p.adam_eps,
+                            weight_decay=p.weight_decay, foreach=False)
+    m = np.zeros_like(W)
+    v = np.zeros_like(W)
+    for t in range(5):
+        grad = oracle.color_gradient(g, K, p, oracle.gamma(MIS, p, t), W)
+        wt.grad = torch.tensor(grad, dtype=torch.float64)
+        opt.step()
+        out = oracle.color_step(g, K, p, t, W, m, v)
+        W, m, v = out.X, out.m, out.v
+        assert 0.0 < W.min() and W.max() < 1.0
+        np.testing.assert_allclose(W, wt.detach().numpy(), rtol=1e-13, atol=1e-15)
+    pT = p.with_(temperature=0.01)
+    a = oracle.color_step(g, K, p, 2, W, m, v)
+    b = oracle.color_step(g, K, pT, 2, W, m, v)
+    xi = np.array([[[oracle.gaussian(p.seed, i * K + k, s, 2) for s in range(p.S)] for k in range(K)]
+                   for i in range(g.n)])
+    np.testing.assert_allclose(b.X - a.X, math.sqrt(2 * p.lr * 0.01) * xi, atol=1e-14)
+    big = oracle.color_step(g, K, p.with_(lr=30.0, temperature=4.0), 2, W, m, v)
+    assert big.X.min() >= 0.0 and big.X.max() <= 1.0 and np.any(big.X == 0.0) and np.any(big.X == 1.0)
+
+
+def test_color_init_and_rounding_rules(oracle_lib):
+    """W starts as the U(0,1] draw of counter row i*K + k; rounding takes the
+    colour of the largest sigma (lowest colour on ties) and the best replica has
+    the fewest conflicts (lowest index on ties)."""
+    g = G.erdos_renyi(10, 0.4, 5)
+    K, S = 3, 4
+    W = oracle.color_init(g.n, K, S, 77)
+    for (i, k, s) in [(0, 0, 0), (3, 2, 1), (9, 1, 3)]:
+        assert W[i, k, s] == oracle.uniform(77, i * K + k, s, 0, 0)
+    W2 = np.zeros((g.n, K, S))
+    W2[:, 1, :] = 0.5
+    W2[:, 2, :] = 0.5          # tie between colours 1 and 2 -> 1
+    W2[0, :, 0] = 0.0          # a zero row is uniform -> colour 0
+    x, conf, best = oracle.color_round(g, K, W2)
+    assert x[0, 0] == 0 and np.all(x[1:, 0] == 1) and np.all(x[:, 1:] == 1)
+    assert conf[1] == g.nnz // 2 and best == int(np.argmin(conf))
+
+
+def test_color_anneal_matches_brute_force_on_tiny_graphs(oracle_lib):
+    """On 20 random graphs of 7 nodes, the oracle anneal (S = 8, 600 steps)
+    reaches the brute-force minimum number of conflicts with 3 colours on at
+    least 90% of them."""
+    hits = 0
+    for seed in range(20):
+        g = G.erdos_renyi(7, 0.55, 300 + seed)
+        best_bf = min(oracle.color_conflicts(g, np.array(x)) for x in itertools.product(range(3), repeat=g.n))
+        conf, best, _, _ = oracle.color_anneal(g, 3, Params(S=8, steps=600, seed=seed, lr=0.1))
+        hits += int(conf[best] == best_bf)
+    assert hits >= 18
+
+
+@pytest.mark.parametrize("name", ["queen5-5", "queen6-6", "myciel5"])
+def test_color_anneal_reaches_the_papers_conflicts(oracle_lib, name):
+    """The oracle anneal reaches the conflict count PQQA reports in Table 6 (a
+    proper colouring with the colours of Table 9)."""
+    row = [r for r in _color_graphs() if r[0] == name][0]
+    g = _make_color_graph(row[1])
+    conf, best, _, _ = oracle.color_anneal(g, row[4], Params(S=32, steps=2000, seed=1, lr=0.1))
+    assert conf[best] <= row[5]

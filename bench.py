@@ -664,6 +664,54 @@ def run_ablation(args):
     return 0
 
 
+# ------------------------------------------------------------------ colouring
+def run_coloring(args):
+    """Categorical PQQA on the generated graph-colouring instances of Table 9
+    (Mycielski and queens graphs, the paper's colour counts): S replicas,
+    a full schedule per seed, the best conflicts reached (Table 6 reports
+    PQQA's), the device time of the anneal and its replica-steps/s. One JSON
+    line per graph, then one summary line."""
+    import torch
+    import paper_2409_02135_gb300 as qqa
+    stream = torch.cuda.current_stream()
+    S, steps, seeds = args.color_S, args.color_steps, args.color_seeds
+    paper = {}
+    gold = os.path.join(ROOT, "tests", "golden", "paper_color_graphs.txt")
+    with open(gold) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                paper[parts[0]] = int(parts[5])
+    total_rs, total_s = 0.0, 0.0
+    for name, make, K in W.COLOR_GRAPHS:
+        g = make()
+        best, times = [], []
+        for seed in range(seeds):
+            p = W.Params(S=S, steps=steps, lr=args.color_lr, seed=seed, precision=W.FP32)
+            c = qqa.Coloring(g, K, qqa.make_params(p), stream=stream)
+            c.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.steps(steps)
+            e1.record(stream)
+            r = c.round(with_x=False)
+            times.append(e0.elapsed_time(e1) / 1e3)
+            best.append(int(r["conflicts"][r["best_s"]]))
+            c.close()
+        dt = statistics.mean(times)
+        total_rs += S * steps * seeds
+        total_s += sum(times)
+        print(json.dumps({"coloring": name, "n": g.n, "edges": g.nnz // 2, "K": K, "S": S, "steps": steps,
+                          "seeds": seeds, "lr": args.color_lr, "best_conflicts": best, "min_conflicts": min(best),
+                          "paper_pqqa_conflicts": paper.get(name), "anneal_s": dt,
+                          "replica_steps_per_s": S * steps / dt}), flush=True)
+    print(json.dumps({"metric": "coloring_replica_steps_per_s", "value": total_rs / total_s,
+                      "unit": "replica-steps/s", "graphs": len(W.COLOR_GRAPHS), "S": S, "steps": steps,
+                      "seeds": seeds, "dtype": "f32", "data": "synthetic (graphs built from their definitions)"}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,7 +720,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="mis_er700_800",
                     help="mis_er700_800 (default), mis_er100, maxcut_regular3, maxcut_ba4, mis_cliqueblocks512, "
-                         "serving, or mis_rrg_d<d>_n<n>[_x<graphs>][_K<steps>] (S = 1 random regular graphs)")
+                         "serving, coloring (Table 9 graphs), or mis_rrg_d<d>_n<n>[_x<graphs>][_K<steps>] "
+                         "(S = 1 random regular graphs)")
     ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense", "pipe"], default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
@@ -690,7 +739,13 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--ablation", choices=["schedule", "gamma0", "alpha"], default=None,
                     help="run one of the paper's ablation sweeps instead of the benchmark")
+    ap.add_argument("--color-S", type=int, default=1024)
+    ap.add_argument("--color-steps", type=int, default=3000)
+    ap.add_argument("--color-seeds", type=int, default=3)
+    ap.add_argument("--color-lr", type=float, default=0.1)
     args = ap.parse_args()
+    if args.workload == "coloring":
+        return run_coloring(args)
     if args.ablation:
         return run_ablation(args)
     if args.warmup < 3 and args.impl == "ours":

@@ -366,6 +366,65 @@ int qqa_round_eval_noalloc(int32_t kind, int32_t n, int64_t nnz, const int32_t *
                            int64_t *viol, uint8_t *feasible, double *energy, int32_t *best_s, void *stream);
 const char *qqa_noalloc_last_error(void);
 
+/* ------------------------------------------------ categorical colouring */
+/*
+ * Categorical PQQA for graph colouring with K colours (App. B, App. C.4, and
+ * the colouring problem of App. D.1 read as minimising the number of
+ * conflicting edges). One instance of n nodes and S replicas; the variables
+ * are W[i][k][s] in [0,1] and the relaxation is
+ *   sigma_ik = W_ik / sum_k' W_ik'   (Clamp-normalise, App. C.4; 1/K for a zero row).
+ * One step, for every node i, colour k and replica s:
+ *   g_ik = sum_{j in N(i)} sigma_jk                      relaxed conflicts
+ *        + gamma_t (-c_K a K) (K sigma_ik - 1)^(a-1)     categorical alpha-entropy s_K (App. B),
+ *                                                        c_K = 1 / ((K-1)((K-1)^(a-1) + 1))
+ *        - alpha (sigma_ik - mean_ik) / STD_ik           communication term of Eq. 10 per (i, k)
+ *   dR/dW_ik = (g_ik - sum_k' sigma_ik' g_ik') / sum_k' W_ik'
+ *   W <- AdamW(W, dR/dW) + sqrt(2 lr T) xi, then clamp to [0, 1]   (as the binary step)
+ * with gamma_t on the linear schedule of App. C.2 over prm->steps steps, and
+ * xi / the initial W from the binary method's Philox streams with counter row
+ * i*K + k. Rounding: x_is = argmax_k sigma_iks (ties to the lowest colour);
+ * the cost of a replica is its number of edges {i, j} with x_is = x_js.
+ * The state lives in device memory owned by the handle: W, m, v and two
+ * buffers of sigma, each n * K * ceil(S/32)*32 floats. FP32 only.
+ */
+#define QQA_COLOR_MAX_K 32
+typedef struct qqa_color qqa_color;
+
+/*
+ * Create an instance and draw the initial W (U(0,1], m = v = 0, t = 0).
+ *   n, row_ptr, col : HOST CSR graph, validated as for qqa_create_problem
+ *                     (symmetric, sorted rows, no self-loops; unit weights)
+ *   K               : colours, 2..QQA_COLOR_MAX_K
+ *   prm             : S (1..1024), steps (>= 1), a_ent, lr, weight_decay,
+ *                     beta1, beta2, adam_eps, gamma_min, gamma_max,
+ *                     alpha_comm, comm_eps, temperature, seed; precision
+ *                     must be QQA_FP32; lambda and round_every are unused
+ *   stream          : cudaStream_t every later call on the handle uses
+ * QQA_EINVAL for bad arguments, QQA_ENOMEM / QQA_ECUDA on device failures.
+ */
+int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t K, const qqa_params *prm,
+                     void *stream, qqa_color **out);
+void qqa_color_destroy(qqa_color *c);
+/* Enqueue up to nsteps steps (fewer when the schedule ends); *done (optional)
+ * receives the count. Asynchronous. */
+int qqa_color_steps(qqa_color *c, int32_t nsteps, int32_t *done);
+/* Wait for the stream; QQA_ENONFINITE if a step produced a non-finite moment. */
+int qqa_color_sync(qqa_color *c);
+/* One step that also writes dR/dW of that step to the HOST array grad[n][K][S]. */
+int qqa_color_step_debug(qqa_color *c, float *grad);
+/* HOST copies [n][K][S] (element ((i*K + k)*S + s)) of W, m, v (any may be
+ * NULL) and the step counter. Synchronous. */
+int qqa_color_get_state(qqa_color *c, float *W, float *m, float *v, int32_t *t);
+/* Replace the state from HOST arrays in the same layout; W must lie in
+ * [0, 1], m be finite and v >= 0 (else QQA_EINVAL); 0 <= t <= prm->steps. */
+int qqa_color_set_state(qqa_color *c, const float *W, const float *m, const float *v, int32_t t);
+/* Round every replica and count its conflicts: conflicts: HOST int64[S];
+ * best_s: the replica with the fewest conflicts (ties: lowest s); x_all
+ * (optional): HOST uint8[n][S] colours. Synchronous. */
+int qqa_color_round(qqa_color *c, int64_t *conflicts, int32_t *best_s, uint8_t *x_all);
+/* Shape and step counter of the handle (any pointer may be NULL). */
+int qqa_color_info(const qqa_color *c, int32_t *n, int32_t *K, int32_t *S, int32_t *t);
+
 #ifdef __cplusplus
 }
 #endif

@@ -606,7 +606,10 @@ void oracle_color_gradient(const oracle_params *P, int32_t n, int32_t K, const i
                 double ent = gamma * (-cK * (double)P->a_ent * (double)K * ipow((double)K * sig - 1.0, P->a_ent - 1));
                 double comm = P->alpha_comm != 0.0 ? -P->alpha_comm * (sig - mean[k]) / std[k] : 0.0;
                 gs[k] = y + ent + comm;
-                as[k] = fabs(y) + fabs(ent) + fabs(comm);
+                /* scale of the communication term: sigma and its mean are rounded before
+                   they are subtracted, as in the binary gradient's scale */
+                double comm_scale = P->alpha_comm != 0.0 ? P->alpha_comm * (fabs(sig) + fabs(mean[k])) / std[k] : 0.0;
+                as[k] = fabs(y) + fabs(ent) + comm_scale;
                 dot += sig * gs[k];
                 adot += sig * as[k];
             }

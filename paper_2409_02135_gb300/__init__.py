@@ -25,7 +25,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = ["Problem", "Run", "Server", "anneal", "autotune", "make_params", "LaunchConfig", "QQAError", "MIS",
            "MAXCUT", "MAXCLIQUE", "FP32", "BF16", "launch_count", "torch_allocator", "stream_handle",
-           "request_bytes", "round_eval_noalloc"]
+           "request_bytes", "round_eval_noalloc", "Coloring", "color_anneal"]
 
 
 def _ptr(a, ctype):
@@ -387,3 +387,76 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Coloring:
+    """Categorical PQQA for graph colouring with K colours (qqa_color_*):
+    state W[n][K][S] in [0, 1], relaxation sigma = W / sum_k W (App. B, C.4)."""
+
+    def __init__(self, graph, K: int, params, stream=None):
+        self.n, self.K = int(graph.n), int(K)
+        rp = np.ascontiguousarray(graph.row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(graph.col, dtype=np.int32)
+        self.params = make_params(params) if not isinstance(params, qqa_params) else params
+        self.S = int(self.params.S)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        check(load().qqa_color_create(self.n, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32), self.K,
+                                      ctypes.byref(self.params), stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def steps(self, nsteps: int) -> int:
+        done = ctypes.c_int32()
+        check(load().qqa_color_steps(self.handle, int(nsteps), ctypes.byref(done)))
+        return int(done.value)
+
+    def sync(self):
+        check(load().qqa_color_sync(self.handle))
+
+    def step_debug(self):
+        g = np.empty((self.n, self.K, self.S), np.float32)
+        check(load().qqa_color_step_debug(self.handle, _ptr(g, ctypes.c_float)))
+        return g
+
+    def get_state(self):
+        W, m, v = (np.empty((self.n, self.K, self.S), np.float32) for _ in range(3))
+        t = ctypes.c_int32()
+        check(load().qqa_color_get_state(self.handle, _ptr(W, ctypes.c_float), _ptr(m, ctypes.c_float),
+                                         _ptr(v, ctypes.c_float), ctypes.byref(t)))
+        return W, m, v, int(t.value)
+
+    def set_state(self, W, m, v, t: int):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32).reshape(self.n, self.K, self.S) for a in (W, m, v)]
+        check(load().qqa_color_set_state(self.handle, *(_ptr(a, ctypes.c_float) for a in arrs), int(t)))
+
+    def round(self, with_x: bool = True) -> dict:
+        conf = np.empty(self.S, np.int64)
+        best = ctypes.c_int32()
+        x = np.empty((self.n, self.S), np.uint8) if with_x else None
+        check(load().qqa_color_round(self.handle, _ptr(conf, ctypes.c_int64), ctypes.byref(best),
+                                     _ptr(x, ctypes.c_uint8)))
+        return {"conflicts": conf, "best_s": int(best.value), "x": x}
+
+    @property
+    def t(self) -> int:
+        t = ctypes.c_int32()
+        check(load().qqa_color_info(self.handle, None, None, None, ctypes.byref(t)))
+        return int(t.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qqa_color_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def color_anneal(graph, K: int, params, stream=None) -> tuple[Coloring, dict]:
+    """Initial draw, the full schedule of params.steps steps, and the rounding."""
+    c = Coloring(graph, K, params, stream=stream)
+    c.steps(c.params.steps)
+    return c, c.round()

@@ -107,6 +107,15 @@ SIGNATURES = {
     "qqa_round_eval_noalloc": (ctypes.c_int, [_I32, _I32, ctypes.c_int64, _P, _P, _P, _I32, ctypes.c_int64, _P,
                                               ctypes.c_float, _P, _P, _P, _P, _P, _P]),
     "qqa_noalloc_last_error": (ctypes.c_char_p, []),
+    "qqa_color_create": (ctypes.c_int, [_I32, _PI32, _PI32, _I32, _PPARAMS, _P, _PP]),
+    "qqa_color_destroy": (None, [_P]),
+    "qqa_color_steps": (ctypes.c_int, [_P, _I32, _PI32]),
+    "qqa_color_sync": (ctypes.c_int, [_P]),
+    "qqa_color_step_debug": (ctypes.c_int, [_P, _PF]),
+    "qqa_color_get_state": (ctypes.c_int, [_P, _PF, _PF, _PF, _PI32]),
+    "qqa_color_set_state": (ctypes.c_int, [_P, _PF, _PF, _PF, _I32]),
+    "qqa_color_round": (ctypes.c_int, [_P, _PI64, _PI32, _PU8]),
+    "qqa_color_info": (ctypes.c_int, [_P, _PI32, _PI32, _PI32, _PI32]),
     "qqa_request_bytes": (ctypes.c_int64, [_I32, ctypes.c_int64, _I32, _I32, _I32]),
     "qqa_server_create": (ctypes.c_int, [ctypes.c_int64, _I32, _I32, _I32, _PCFG, _PALLOC, _PP]),
     "qqa_server_submit": (ctypes.c_int, [_P, _I32, _I32, _PI32, _PI32, _PI32, _PPARAMS, _PI64]),

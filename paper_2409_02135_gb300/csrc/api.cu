@@ -174,6 +174,14 @@ static int validate_csr(int32_t kind, int32_t n, const int32_t *rp, const int32_
     return QQA_OK;
 }
 
+// Shared with the colouring entry points (color.cu): the error slot, the
+// graph checks (unit weights) and the launch counter of this library.
+namespace qqa {
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+int check_unit_graph(int32_t n, const int32_t *rp, const int32_t *col) { return validate_csr(QQA_MIS, n, rp, col, nullptr); }
+void add_launches(unsigned long long k) { g_launches += k; }
+}  // namespace qqa
+
 extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_ptr, const int32_t *col,
                                   const int32_t *w, const qqa_allocator *alloc, void *stream, qqa_problem **out)
 {

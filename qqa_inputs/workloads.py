@@ -185,3 +185,20 @@ def serving_trace(num: int = 2000, rate_per_s: float = 200.0, seed: int = 9, n_l
 def graph_from_spec(spec) -> G.CSRGraph:
     kind, n, avg_degree, gseed = spec
     return G.erdos_renyi_avg_degree(n, avg_degree, gseed)
+
+
+# Graph colouring instances of the paper's Table 9 that have a definition
+# (Mycielski and queens graphs; the book graphs are dataset files): name,
+# generator and the number of colours K the paper runs them with.
+COLOR_GRAPHS = [
+    ("myciel5", lambda: G.mycielski(5), 6),
+    ("myciel6", lambda: G.mycielski(6), 7),
+    ("queen5-5", lambda: G.queens(5, 5), 5),
+    ("queen6-6", lambda: G.queens(6, 6), 7),
+    ("queen7-7", lambda: G.queens(7, 7), 7),
+    ("queen8-8", lambda: G.queens(8, 8), 9),
+    ("queen9-9", lambda: G.queens(9, 9), 10),
+    ("queen8-12", lambda: G.queens(8, 12), 12),
+    ("queen11-11", lambda: G.queens(11, 11), 11),
+    ("queen13-13", lambda: G.queens(13, 13), 13),
+]

@@ -39,6 +39,7 @@ from qqa_inputs import workloads as W  # noqa: E402
 
 METRIC = "replica-steps/s"
 BYTES_PER_ELEMENT_STEP = {W.FP32: 24, W.BF16: 20}   # compulsory HBM bytes of one (node, replica) update
+COLOR_BYTES_PER_ELEMENT_STEP = 32                     # one (node, colour, replica) of the colouring step
 
 
 def build_workload(name: str, rank: int):
@@ -683,7 +684,8 @@ def run_coloring(args):
                 parts = line.split()
                 paper[parts[0]] = int(parts[5])
     total_rs, total_s = 0.0, 0.0
-    for name, make, K in W.COLOR_GRAPHS:
+    chosen = [row for row in W.COLOR_GRAPHS if not args.color_graphs or row[0] in args.color_graphs.split(",")]
+    for name, make, K in chosen:
         g = make()
         best, times = [], []
         for seed in range(seeds):
@@ -691,9 +693,11 @@ def run_coloring(args):
             c = qqa.Coloring(g, K, qqa.make_params(p), stream=stream)
             c.sync()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = qqa.launch_count()
             e0.record(stream)
             c.steps(steps)
             e1.record(stream)
+            launches = (qqa.launch_count() - l0) / steps
             r = c.round(with_x=False)
             times.append(e0.elapsed_time(e1) / 1e3)
             best.append(int(r["conflicts"][r["best_s"]]))
@@ -701,12 +705,17 @@ def run_coloring(args):
         dt = statistics.mean(times)
         total_rs += S * steps * seeds
         total_s += sum(times)
+        step_s = dt / steps
+        state_bytes = COLOR_BYTES_PER_ELEMENT_STEP * g.n * K * S      # W, m, v read + write, sigma read + write
+        gather_bytes = 4 * g.nnz * K * S                               # neighbours' sigma, from L2
         print(json.dumps({"coloring": name, "n": g.n, "edges": g.nnz // 2, "K": K, "S": S, "steps": steps,
                           "seeds": seeds, "lr": args.color_lr, "best_conflicts": best, "min_conflicts": min(best),
                           "paper_pqqa_conflicts": paper.get(name), "anneal_s": dt,
-                          "replica_steps_per_s": S * steps / dt}), flush=True)
+                          "replica_steps_per_s": S * steps / dt, "us_per_step": step_s * 1e6,
+                          "state_GBps": state_bytes / step_s / 1e9, "gather_GBps": gather_bytes / step_s / 1e9,
+                          "launches_per_step": launches}), flush=True)
     print(json.dumps({"metric": "coloring_replica_steps_per_s", "value": total_rs / total_s,
-                      "unit": "replica-steps/s", "graphs": len(W.COLOR_GRAPHS), "S": S, "steps": steps,
+                      "unit": "replica-steps/s", "graphs": len(chosen), "S": S, "steps": steps,
                       "seeds": seeds, "dtype": "f32", "data": "synthetic (graphs built from their definitions)"}),
           flush=True)
     return 0
@@ -743,6 +752,7 @@ def main():
     ap.add_argument("--color-steps", type=int, default=3000)
     ap.add_argument("--color-seeds", type=int, default=3)
     ap.add_argument("--color-lr", type=float, default=0.1)
+    ap.add_argument("--color-graphs", default="", help="comma-separated subset of the colouring graphs")
     args = ap.parse_args()
     if args.workload == "coloring":
         return run_coloring(args)

@@ -7,14 +7,22 @@
 // [0,1]). Rows of one (i, k) are S_pad = S rounded up to 32 floats long, so a
 // warp reads 128 contiguous bytes of one colour plane.
 //
-// One step (color_step_kernel, one block per node, replicas across threads):
-//   statistics  mean_ik, STD_ik = sqrt(var_ik + eps) of sigma over replicas (Eq. 10)
-//   gradient    g_ik = sum_{j in N(i)} sigma_jk                       relaxed conflicts
-//                    + gamma_t (-c_K a K) (K sigma_ik - 1)^(a-1)      entropy s_K (App. B)
-//                    - alpha (sigma_ik - mean_ik) / STD_ik            communication (Eq. 10)
-//               dR/dW_ik = (g_ik - sum_k' sigma_ik' g_ik') / sum_k W_ik   (Clamp-normalise chain rule)
-//   update      AdamW with decoupled decay, + sqrt(2 lr T) xi, projection to [0,1]
-//   relaxation  sigma' = W' / sum_k W' (a zero row: 1/K), into the other buffer
+// One step is two launches:
+//   color_gather_kernel  Y = A sigma, the neighbour sums of the relaxed
+//                        conflicts, as a sparse-times-dense product over the
+//                        columns (k, s) of sigma staged in shared memory
+//                        (graphs of up to 1600 nodes; larger graphs gather
+//                        from global memory inside the update kernel)
+//   color_update_kernel  one block per node, four replicas per thread:
+//     gradient    g_ik = Y_ik                                           relaxed conflicts
+//                      + gamma_t (-c_K a K) (K sigma_ik - 1)^(a-1)      entropy s_K (App. B)
+//                      - alpha (sigma_ik - mean_ik) / STD_ik            communication (Eq. 10)
+//                 dR/dW_ik = (g_ik - sum_k' sigma_ik' g_ik') / sum_k W_ik   (Clamp-normalise chain rule)
+//     update      AdamW with decoupled decay, + sqrt(2 lr T) xi, projection to [0,1]
+//     relaxation  sigma' = W' / sum_k W' (a zero row: 1/K), into the other buffer,
+//                 with the row sums sum_k W' for the next chain rule
+//     statistics  mean and STD_eps of sigma' over the replicas of each (i, k)
+//                 for the next step's communication term (two block reductions)
 // sigma is double-buffered: a step reads sigma^t of the neighbours and writes
 // sigma^{t+1} of its own node, so every block sees one consistent state.
 //
@@ -28,6 +36,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/qqa.h"
@@ -43,8 +52,6 @@ using namespace qqa;
 
 namespace {
 
-constexpr int kColorThreads = 256;       // block of the step kernel (replicas strided over it)
-constexpr int kColorWarps = kColorThreads / 32;
 
 int cfail(int code, const char *fmt, ...)
 {
@@ -62,170 +69,251 @@ int cfail(int code, const char *fmt, ...)
         if (e_ != cudaSuccess) return cfail(QQA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
-// Per-step scalars, computed on the host in double and rounded once.
+// Arguments of one step. The step index is t = *t_dev + r: the device counter
+// t_dev advances after every chunk of steps (so one captured CUDA graph serves
+// every chunk of the same length) and r is the step's offset in its chunk.
+// sched[t] = (gamma_t (-c_K a K), lr / (1 - b1^(t+1)), 1 / sqrt(1 - b2^(t+1)))
+// is computed on the host in double and rounded once.
 struct ColorStepArgs {
-    int32_t n, K, S, S_pad, t, half_pow;
-    float ent_coef;       // gamma_t * (-c_K a K)
-    float step_size;      // lr / (1 - b1^(t+1))
-    float inv_sqrt_bc2;   // 1 / sqrt(1 - b2^(t+1))
+    int32_t n, K, S, S_pad, half_pow, r;
+    const int32_t *t_dev;
+    const float4 *sched;
     float decay;          // 1 - lr * weight_decay
     float b1, b2, adam_eps, alpha, comm_eps, noise_scale;
     uint32_t seed_lo, seed_hi;
 };
 
-// Sum of v[k] over the block for every k < KMAX; every thread gets the totals in out[].
-template <int KMAX>
-__device__ __forceinline__ void block_sum(float (&v)[KMAX], float (*part)[KMAX], float *out, int K)
+// Replica statistics of sigma for the communication term (Eq. 10), one warp
+// per (node, colour) row: mean over the S replicas, then the population
+// variance as the mean of squared deviations (two passes; the second reads
+// the row from L1). stat[r] = (mean, -alpha / sqrt(var + eps)).
+__global__ void __launch_bounds__(256) color_stats_kernel(int32_t rows, int32_t S, int32_t S_pad, float alpha,
+                                                          float comm_eps, const float *__restrict__ sig0,
+                                                          const float *__restrict__ sig1,
+                                                          const int32_t *__restrict__ t_dev, int32_t step_off,
+                                                          float2 *__restrict__ stat)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float *__restrict__ sig = ((*t_dev + step_off) & 1) ? sig1 : sig0;
+    const float *row = sig + (size_t)r * S_pad;
+    float acc = 0.0f;
+    for (int s = lane; s < S; s += 32) acc += row[s];
 #pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        if (k >= K) break;
-        float x = v[k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const float mean = acc / (float)S;
+    float ss = 0.0f;
+    for (int s = lane; s < S; s += 32) {
+        const float d = row[s] - mean;
+        ss = fmaf(d, d, ss);
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) part[warp][k] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        float acc = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += part[w][threadIdx.x];
-        out[threadIdx.x] = acc;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) stat[r] = make_float2(mean, -alpha / sqrtf(fmaf(ss, 1.0f / (float)S, comm_eps)));
 }
 
-// Standard normal of (counter row, replica s, step t): element s mod 4 of the
-// Box-Muller quad of Philox block (row, s/4, t, 1), the binary method's stream.
-__device__ __forceinline__ float color_gauss(uint32_t lo, uint32_t hi, uint32_t row, int s, uint32_t t)
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, const float (&v)[4])
 {
-    const U4 r = philox10(U4{row, (uint32_t)(s >> 2), t, 1u}, lo, hi);
-    const int e = s & 3;
-    float z0, z1;
-    if (e < 2) box_muller(r.x, r.y, z0, z1);
-    else box_muller(r.z, r.w, z0, z1);
-    return (e & 1) ? z1 : z0;
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(kColorThreads)
-color_step_kernel(ColorStepArgs a, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                  const float *__restrict__ sig_cur, float *__restrict__ sig_next, float *__restrict__ W,
-                  float *__restrict__ M, float *__restrict__ V, float *__restrict__ grad_dbg,
-                  unsigned long long *__restrict__ nonfinite)
+// The step of node i = blockIdx.x / chunks for replica quads q = 32 c + lane,
+// c = blockIdx.x % chunks: warp k of the block (K warps) owns colour k, so
+// every access is a coalesced 16-byte-per-lane row of one (i, k) plane. The
+// sums over colours (sum_k sigma_k g_k of the chain rule, sum_k W'_k of the
+// next relaxation) meet in shared memory. stat[i*K + k] = (mean, -alpha /
+// STD) of this step (unused when alpha = 0); rsum[i][s] holds sum_k W of this
+// step on entry and of the next on exit. Ygat is NULL for graphs too large
+// for color_gather_kernel: the neighbour sums are then gathered here.
+__global__ void __launch_bounds__(1024)
+color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                    const float2 *__restrict__ stat, const float *__restrict__ Ygat, float *__restrict__ sig0,
+                    float *__restrict__ sig1, float *__restrict__ W, float *__restrict__ M,
+                    float *__restrict__ V, float *__restrict__ rsum, float *__restrict__ grad_dbg,
+                    unsigned long long *__restrict__ nonfinite)
 {
-    __shared__ float part[kColorWarps][KMAX];
-    __shared__ float sh_mean[KMAX], sh_ss[KMAX];
-    const int K = a.K, S = a.S;
+    const int t = *a.t_dev + a.r;
+    const float4 sc = a.sched[t];   // (entropy coefficient, step size, 1 / sqrt(bc2))
+    const float *__restrict__ sig_cur = (t & 1) ? sig1 : sig0;
+    float *__restrict__ sig_next = (t & 1) ? sig0 : sig1;
+    __shared__ float4 xk[32][32];   // [colour][lane]: sigma_k g_k, then W'_k
+    const int K = a.K;
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = (int)(blockIdx.x / (unsigned)chunks);
+    const int q = (int)(blockIdx.x % (unsigned)chunks) * 32 + lane, s0 = 4 * q;
+    const bool live = s0 < a.S;
     const size_t plane = (size_t)a.S_pad, node = (size_t)K * plane;
-    const float inv_S = 1.0f / (float)S;
-    const float om_b1 = 1.0f - a.b1, om_b2 = 1.0f - a.b2;
+    const size_t idx = (size_t)i * node + (size_t)k * plane + s0;
     const float fK = (float)K;
 
-    for (int i = blockIdx.x; i < a.n; i += gridDim.x) {
-        const float *__restrict__ sig_i = sig_cur + (size_t)i * node;
-        // population mean and variance of sigma_ik over the replicas (two passes)
-        float acc[KMAX];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) acc[k] = 0.0f;
-        for (int s = threadIdx.x; s < S; s += blockDim.x) {
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < K) acc[k] += sig_i[k * plane + s];
-        }
-        block_sum<KMAX>(acc, part, sh_mean, K);
-        float mean[KMAX];
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            mean[k] = k < K ? sh_mean[k] * inv_S : 0.0f;
-            acc[k] = 0.0f;
-        }
-        for (int s = threadIdx.x; s < S; s += blockDim.x) {
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k)
-                if (k < K) {
-                    const float d = sig_i[k * plane + s] - mean[k];
-                    acc[k] = fmaf(d, d, acc[k]);
-                }
-        }
-        block_sum<KMAX>(acc, part, sh_ss, K);
-        float comm[KMAX];   // -alpha / STD_ik
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-            comm[k] = k < K ? -a.alpha / sqrtf(fmaf(sh_ss[k], inv_S, a.comm_eps)) : 0.0f;
-
-        const int e0 = rp[i], e1 = rp[i + 1];
-        for (int s = threadIdx.x; s < S; s += blockDim.x) {
-            float sg[KMAX], y[KMAX];
-            float wsum = 0.0f;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                sg[k] = k < K ? sig_i[k * plane + s] : 0.0f;
-                wsum += k < K ? W[(size_t)i * node + k * plane + s] : 0.0f;
-                y[k] = 0.0f;
-            }
-            // relaxed conflicts: sum of the neighbours' sigma of the same colour
-            for (int e = e0; e < e1; ++e) {
-                const float *__restrict__ sj = sig_cur + (size_t)__ldg(col + e) * node + s;
-#pragma unroll
-                for (int k = 0; k < KMAX; ++k)
-                    if (k < K) y[k] += sj[k * plane];
-            }
-            // dR/dsigma, then the chain rule through W / sum W
-            float dot = 0.0f;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                if (k >= K) break;
-                const float u = fmaf(fK, sg[k], -1.0f);
-                const float u2 = u * u;
-                float upow = u;
-                for (int h = 0; h < a.half_pow; ++h) upow *= u2;
-                float g = fmaf(a.ent_coef, upow, y[k]);
-                g = fmaf(comm[k], sg[k] - mean[k], g);
-                y[k] = g;
-                dot = fmaf(sg[k], g, dot);
-            }
-            const float inv_w = wsum > 0.0f ? 1.0f / wsum : 0.0f;
-            float wn[KMAX];
-            float nsum = 0.0f, vsum = 0.0f;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                if (k >= K) break;
-                const size_t idx = (size_t)i * node + k * plane + s;
-                const float g = (y[k] - dot) * inv_w;
-                if (grad_dbg) grad_dbg[idx] = g;
-                const float mn = fmaf(a.b1, M[idx], om_b1 * g);
-                const float vn = fmaf(a.b2, V[idx], om_b2 * (g * g));
-                const float denom = fmaf(sqrtf(vn), a.inv_sqrt_bc2, a.adam_eps);
-                float q = W[idx] * a.decay;
-                q = fmaf(-a.step_size, mn / denom, q);
-                const float xi = a.noise_scale != 0.0f
-                                     ? color_gauss(a.seed_lo, a.seed_hi, (uint32_t)(i * K + k), s, (uint32_t)a.t)
-                                     : 0.0f;
-                const float w = __saturatef(fmaf(a.noise_scale, xi, q));
-                M[idx] = mn;
-                V[idx] = vn;
-                W[idx] = w;
-                wn[k] = w;
-                nsum += w;
-                vsum += vn;
-            }
-            if (!(vsum <= 3.0e38f)) atomicAdd(nonfinite, 1ULL);
-            const float inv_n = nsum > 0.0f ? 1.0f / nsum : 0.0f;
-            float *__restrict__ out = sig_next + (size_t)i * node + s;
-#pragma unroll
-            for (int k = 0; k < KMAX; ++k) {
-                if (k >= K) break;
-                out[k * plane] = nsum > 0.0f ? wn[k] * inv_n : 1.0f / fK;
+    float g[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) {
+        // relaxed conflicts Y_ik
+        if (Ygat) {
+            const float4 y = ld4(Ygat + idx);
+            g[0] = y.x, g[1] = y.y, g[2] = y.z, g[3] = y.w;
+        } else {
+            const float *__restrict__ base = sig_cur + (size_t)k * plane + s0;
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const float4 y = ld4(base + (size_t)__ldg(col + e) * node);
+                g[0] += y.x, g[1] += y.y, g[2] += y.z, g[3] += y.w;
             }
         }
-        __syncthreads();   // shared statistics are rewritten by the next node
+        const float4 sv = ld4(sig_cur + idx);
+        sg[0] = sv.x, sg[1] = sv.y, sg[2] = sv.z, sg[3] = sv.w;
+        float2 st = make_float2(0.0f, 0.0f);
+        if (a.alpha != 0.0f) st = stat[(size_t)i * K + k];
+        // dR/dsigma: + entropy s_K + communication
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float u = fmaf(fK, sg[e], -1.0f);
+            const float u2 = u * u;
+            float upow = u;
+            for (int h = 0; h < a.half_pow; ++h) upow *= u2;
+            g[e] = fmaf(st.y, sg[e] - st.x, fmaf(sc.x, upow, g[e]));
+        }
+    }
+    xk[k][lane] = make_float4(sg[0] * g[0], sg[1] * g[1], sg[2] * g[2], sg[3] * g[3]);
+    __syncthreads();
+    float dot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int kk = 0; kk < K; ++kk) {
+        const float4 d = xk[kk][lane];
+        dot[0] += d.x, dot[1] += d.y, dot[2] += d.z, dot[3] += d.w;
+    }
+    float wn[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) {
+        // chain rule through W / sum W, AdamW, noise, projection
+        const float4 rs = ld4(rsum + (size_t)i * plane + s0);
+        const float rsv[4] = {rs.x, rs.y, rs.z, rs.w};
+        float xi[4];
+        if (a.noise_scale != 0.0f) gauss4(a.seed_lo, a.seed_hi, (uint32_t)(i * K + k), (uint32_t)q, (uint32_t)t, xi);
+        else xi[0] = xi[1] = xi[2] = xi[3] = 0.0f;
+        const float4 w4 = ld4(W + idx), m4 = ld4(M + idx), v4 = ld4(V + idx);
+        const float w0[4] = {w4.x, w4.y, w4.z, w4.w}, m0[4] = {m4.x, m4.y, m4.z, m4.w},
+                    v0[4] = {v4.x, v4.y, v4.z, v4.w};
+        float gw[4], mn[4], vn[4];
+        float vsum = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            gw[e] = rsv[e] > 0.0f ? (g[e] - dot[e]) / rsv[e] : 0.0f;
+            mn[e] = fmaf(a.b1, m0[e], (1.0f - a.b1) * gw[e]);
+            vn[e] = fmaf(a.b2, v0[e], (1.0f - a.b2) * (gw[e] * gw[e]));
+            const float denom = fmaf(sqrtf(vn[e]), sc.z, a.adam_eps);
+            const float qv = fmaf(-sc.y, mn[e] / denom, w0[e] * a.decay);
+            wn[e] = __saturatef(fmaf(a.noise_scale, xi[e], qv));
+            vsum += vn[e];
+        }
+        if (grad_dbg) st4(grad_dbg + idx, gw);
+        st4(M + idx, mn);
+        st4(V + idx, vn);
+        st4(W + idx, wn);
+        if (!(vsum <= 3.0e38f)) atomicAdd(nonfinite, 1ULL);
+    }
+    __syncthreads();   // every warp has read the products
+    xk[k][lane] = make_float4(wn[0], wn[1], wn[2], wn[3]);
+    __syncthreads();
+    float ns[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int kk = 0; kk < K; ++kk) {
+        const float4 d = xk[kk][lane];
+        ns[0] += d.x, ns[1] += d.y, ns[2] += d.z, ns[3] += d.w;
+    }
+    if (live) {
+        // sigma' = W' / sum_k W' (1/K for a zero row), and the row sums
+        float sp[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sp[e] = ns[e] > 0.0f ? wn[e] * (1.0f / ns[e]) : 1.0f / fK;
+        st4(sig_next + idx, sp);
+        if (k == 0) st4(rsum + (size_t)i * plane + s0, ns);
     }
 }
 
-// sigma = W / sum_k W for every (i, s) (1/K for a zero row).
+// Neighbour sums Y = A sigma of the relaxed conflicts for graphs whose slab
+// fits in shared memory. sigma is read as a matrix [n][C], C = K * S_pad (row
+// j = all colours and replicas of node j). Block b stages the 32 VEC columns
+// [32 VEC c, 32 VEC (c + 1)) of every row, c = b / parts (n * 128 VEC bytes),
+// then each warp sums, for its rows i of part b % parts, the staged rows of
+// i's neighbours, VEC columns per lane. Neighbour indices are read 32 at a
+// time and broadcast by shuffles.
+template <int VEC>
+__global__ void __launch_bounds__(256) color_gather_kernel(int32_t n, int64_t C, int32_t parts,
+                                                           const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ col,
+                                                           const float *__restrict__ sig0,
+                                                           const float *__restrict__ sig1,
+                                                           const int32_t *__restrict__ t_dev, int32_t step_off,
+                                                           float *__restrict__ Y)
+{
+    const float *__restrict__ sig = ((*t_dev + step_off) & 1) ? sig1 : sig0;
+    using V = typename std::conditional<VEC == 4, float4, typename std::conditional<VEC == 2, float2, float>::type>::type;
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    V *slab = reinterpret_cast<V *>(slab_raw);   // [n][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = (int)(blockIdx.x / (unsigned)parts), part = (int)(blockIdx.x % (unsigned)parts);
+    const int64_t c0 = ((int64_t)chunk * 32 + lane) * VEC;
+#pragma unroll 4
+    for (int j = warp; j < n; j += nw) slab[j * 32 + lane] = *reinterpret_cast<const V *>(sig + (int64_t)j * C + c0);
+    __syncthreads();
+    const int rows = (n + parts - 1) / parts;
+    const int r1 = min(n, (part + 1) * rows);
+    for (int i = part * rows + warp; i < r1; i += nw) {
+        const int e0 = rp[i], e1 = rp[i + 1];
+        V y0, y1;
+        if constexpr (VEC == 4) {
+            y0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else if constexpr (VEC == 2) {
+            y0 = make_float2(0.0f, 0.0f);
+        } else {
+            y0 = 0.0f;
+        }
+        y1 = y0;
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int cnt = min(32, e1 - eb);
+            const int mine = lane < cnt ? col[eb + lane] : 0;
+            int qq = 0;
+            for (; qq + 1 < cnt; qq += 2) {
+                const V a0 = slab[__shfl_sync(0xffffffffu, mine, qq) * 32 + lane];
+                const V a1 = slab[__shfl_sync(0xffffffffu, mine, qq + 1) * 32 + lane];
+                if constexpr (VEC == 4) {
+                    y0.x += a0.x, y0.y += a0.y, y0.z += a0.z, y0.w += a0.w;
+                    y1.x += a1.x, y1.y += a1.y, y1.z += a1.z, y1.w += a1.w;
+                } else if constexpr (VEC == 2) {
+                    y0.x += a0.x, y0.y += a0.y;
+                    y1.x += a1.x, y1.y += a1.y;
+                } else {
+                    y0 += a0;
+                    y1 += a1;
+                }
+            }
+            if (qq < cnt) {
+                const V a0 = slab[__shfl_sync(0xffffffffu, mine, qq) * 32 + lane];
+                if constexpr (VEC == 4) {
+                    y0.x += a0.x, y0.y += a0.y, y0.z += a0.z, y0.w += a0.w;
+                } else if constexpr (VEC == 2) {
+                    y0.x += a0.x, y0.y += a0.y;
+                } else {
+                    y0 += a0;
+                }
+            }
+        }
+        if constexpr (VEC == 4)
+            *reinterpret_cast<float4 *>(Y + (int64_t)i * C + c0) =
+                make_float4(y0.x + y1.x, y0.y + y1.y, y0.z + y1.z, y0.w + y1.w);
+        else if constexpr (VEC == 2)
+            *reinterpret_cast<float2 *>(Y + (int64_t)i * C + c0) = make_float2(y0.x + y1.x, y0.y + y1.y);
+        else
+            Y[(int64_t)i * C + c0] = y0 + y1;
+    }
+}
+
+// The step counter of the device: advanced after each chunk, set from the host.
+__global__ void color_advance_kernel(int32_t *t_dev, int32_t by) { *t_dev += by; }
+__global__ void color_set_t_kernel(int32_t *t_dev, int32_t t) { *t_dev = t; }
+
+// sigma = W / sum_k W for every (i, s) (1/K for a zero row), and the row sums.
 __global__ void color_sigma_kernel(int32_t n, int32_t K, int32_t S, int32_t S_pad, const float *__restrict__ W,
-                                   float *__restrict__ sig)
+                                   float *__restrict__ sig, float *__restrict__ rsum)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * S_pad) return;
@@ -238,6 +326,7 @@ __global__ void color_sigma_kernel(int32_t n, int32_t K, int32_t S, int32_t S_pa
     float *o = sig + i * K * S_pad + s;
     const float inv = sum > 0.0f ? 1.0f / sum : 0.0f;
     for (int k = 0; k < K; ++k) o[(int64_t)k * S_pad] = sum > 0.0f ? w[(int64_t)k * S_pad] * inv : 1.0f / (float)K;
+    rsum[idx] = sum;
 }
 
 // W = U(0,1] of Philox block (i*K + k, s/4, 0, 0), element s mod 4 (the binary
@@ -299,16 +388,8 @@ __global__ void color_conflict_kernel(int32_t n, int32_t S, int32_t S_pad, const
     if (c) atomicAdd(conflicts + s, (unsigned long long)c);
 }
 
-using ColorFn = void (*)(ColorStepArgs, const int32_t *, const int32_t *, const float *, float *, float *, float *,
-                         float *, float *, unsigned long long *);
-
-ColorFn color_kernel_for(int K)
-{
-    if (K <= 4) return color_step_kernel<4>;
-    if (K <= 8) return color_step_kernel<8>;
-    if (K <= 16) return color_step_kernel<16>;
-    return color_step_kernel<32>;
-}
+// Largest shared-memory slab of color_gather_kernel (n * 128 VEC bytes).
+constexpr int kGatherSlabMax = 200 * 1024;
 
 }  // namespace
 
@@ -321,9 +402,18 @@ struct qqa_color {
     int sms = 0;
     int32_t *rp = nullptr, *col = nullptr;
     float *W = nullptr, *m = nullptr, *v = nullptr, *sig[2] = {nullptr, nullptr}, *grad = nullptr;
+    float2 *stat = nullptr;   // (mean, -alpha / STD) per (node, colour)
+    float *rsum = nullptr;    // sum_k W per (node, replica)
+    float *Y = nullptr;       // neighbour sums when the graph fits color_gather_kernel's slab
+    int gather_vec = 0;       // 4, 2 or 1: columns per lane of color_gather_kernel; 0: direct gather
+    int32_t *t_dev = nullptr; // step counter of the device
+    float4 *sched = nullptr;  // per-step scalars, [steps]
     uint8_t *x = nullptr;
     unsigned long long *conf = nullptr, *nonfinite = nullptr;
     std::vector<void *> owned;
+    cudaStream_t cap_stream = nullptr;     // private stream the step chunk is captured on
+    cudaGraphExec_t chunk_exec = nullptr;  // kColorChunk steps and the counter advance
+    int chunk_kernels = 0;                 // kernels per replay of chunk_exec
 
     size_t nks() const { return (size_t)n * (size_t)K * (size_t)S_pad; }
 };
@@ -332,6 +422,9 @@ static void color_free(qqa_color *c)
 {
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    if (c->chunk_exec) cudaGraphExecDestroy(c->chunk_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void *p : c->owned) cudaFree(p);
     delete c;
 }
@@ -348,35 +441,34 @@ static T *color_alloc(qqa_color *c, size_t count)
     return (T *)p;
 }
 
+// sigma and the row sums of the current W into buffer `which`.
 static int color_launch_sigma(qqa_color *c, int which)
 {
     const int64_t total = (int64_t)c->n * c->S_pad;
     color_sigma_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->st>>>(c->n, c->K, c->S, c->S_pad, c->W,
-                                                                        c->sig[which]);
+                                                                        c->sig[which], c->rsum);
     COLOR_CK(cudaGetLastError());
     add_launches(1);
     return QQA_OK;
 }
 
-static int color_launch_step(qqa_color *c, float *grad_dbg)
+// Steps replayed per CUDA graph launch.
+constexpr int kColorChunk = 32;
+
+// Enqueue steps t .. t + L - 1 (t = the device counter) on stream st, then
+// advance the counter by L. Returns the number of kernels enqueued, or a
+// negative error code.
+static int color_enqueue_chunk(qqa_color *c, int L, float *grad_dbg, cudaStream_t st)
 {
     const qqa_params &p = c->prm;
-    const int t = c->t;
     ColorStepArgs a{};
     a.n = c->n;
     a.K = c->K;
     a.S = c->S;
     a.S_pad = c->S_pad;
-    a.t = t;
     a.half_pow = (p.a_ent - 2) / 2;
-    const double gamma = p.steps > 1 ? (double)p.gamma_min + ((double)p.gamma_max - (double)p.gamma_min) * (double)t /
-                                                                 (double)(p.steps - 1)
-                                     : (double)p.gamma_min;
-    a.ent_coef = (float)(gamma * (-c->cK * (double)p.a_ent * (double)c->K));
-    const double bc1 = 1.0 - std::pow((double)p.beta1, (double)(t + 1));
-    const double bc2 = 1.0 - std::pow((double)p.beta2, (double)(t + 1));
-    a.step_size = (float)((double)p.lr / bc1);
-    a.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+    a.t_dev = c->t_dev;
+    a.sched = c->sched;
     a.decay = (float)(1.0 - (double)p.lr * (double)p.weight_decay);
     a.b1 = p.beta1;
     a.b2 = p.beta2;
@@ -386,14 +478,89 @@ static int color_launch_step(qqa_color *c, float *grad_dbg)
     a.noise_scale = (float)std::sqrt(2.0 * (double)p.lr * (double)p.temperature);
     a.seed_lo = (uint32_t)(p.seed & 0xffffffffu);
     a.seed_hi = (uint32_t)(p.seed >> 32);
-    const int cur = t & 1;
-    const unsigned grid = (unsigned)std::min<int64_t>(c->n, (int64_t)c->sms * 16);
-    const int threads = std::min(kColorThreads, c->S_pad);
-    color_kernel_for(c->K)<<<grid, threads, 0, c->st>>>(a, c->rp, c->col, c->sig[cur], c->sig[cur ^ 1], c->W, c->m,
-                                                      c->v, grad_dbg, c->nonfinite);
-    COLOR_CK(cudaGetLastError());
-    add_launches(1);
-    c->t = t + 1;
+    int kernels = 0;
+    for (int r = 0; r < L; ++r) {
+        a.r = r;
+        if (p.alpha_comm != 0.0f) {
+            const int rows = c->n * c->K;
+            color_stats_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(rows, c->S, c->S_pad, p.alpha_comm,
+                                                                          p.comm_eps, c->sig[0], c->sig[1], c->t_dev,
+                                                                          r, c->stat);
+            ++kernels;
+        }
+        const float *Ygat = nullptr;
+        if (c->gather_vec) {
+            const int vec = c->gather_vec;
+            const int64_t C = (int64_t)c->K * c->S_pad;
+            const int smem = c->n * 128 * vec;
+            const int64_t chunks = C / (32 * vec);
+            // split the rows so that the blocks fill the GPU in one wave
+            const int64_t per_sm = std::max(1, std::min(8, (228 * 1024) / (smem + 1024)));
+            const int64_t slots = per_sm * c->sms;
+            const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(slots / chunks, (c->n + 31) / 32));
+            const unsigned grid = (unsigned)(chunks * parts);
+            if (vec == 4)
+                color_gather_kernel<4><<<grid, 256, smem, st>>>(c->n, C, parts, c->rp, c->col, c->sig[0], c->sig[1],
+                                                                c->t_dev, r, c->Y);
+            else if (vec == 2)
+                color_gather_kernel<2><<<grid, 256, smem, st>>>(c->n, C, parts, c->rp, c->col, c->sig[0], c->sig[1],
+                                                                c->t_dev, r, c->Y);
+            else
+                color_gather_kernel<1><<<grid, 256, smem, st>>>(c->n, C, parts, c->rp, c->col, c->sig[0], c->sig[1],
+                                                                c->t_dev, r, c->Y);
+            ++kernels;
+            Ygat = c->Y;
+        }
+        const int chunks = (c->S_pad / 4 + 31) / 32;   // 32 quads of replicas per block
+        color_update_kernel<<<(unsigned)((int64_t)c->n * chunks), 32 * c->K, 0, st>>>(
+            a, chunks, c->rp, c->col, c->stat, Ygat, c->sig[0], c->sig[1], c->W, c->m, c->v, c->rsum, grad_dbg,
+            c->nonfinite);
+        ++kernels;
+    }
+    color_advance_kernel<<<1, 1, 0, st>>>(c->t_dev, L);
+    ++kernels;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cfail(QQA_ECUDA, "colouring step launch: %s", cudaGetErrorString(e));
+    return kernels;
+}
+
+// Run L steps: full chunks replay one captured graph (captured on first use
+// on a private stream, launched on the handle's stream), the rest are
+// launched directly.
+static int color_run(qqa_color *c, int L)
+{
+    while (L > 0) {
+        const int len = std::min(L, kColorChunk);
+        if (len == kColorChunk) {
+            if (!c->chunk_exec) {
+                if (!c->cap_stream) COLOR_CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+                cudaGraph_t g = nullptr;
+                COLOR_CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+                const int k = color_enqueue_chunk(c, kColorChunk, nullptr, c->cap_stream);
+                const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+                if (k < 0) {
+                    if (g) cudaGraphDestroy(g);
+                    return k;
+                }
+                if (e != cudaSuccess) return cfail(QQA_ECUDA, "colouring chunk capture: %s", cudaGetErrorString(e));
+                const cudaError_t ei = cudaGraphInstantiate(&c->chunk_exec, g, 0);
+                cudaGraphDestroy(g);
+                if (ei != cudaSuccess) {
+                    c->chunk_exec = nullptr;
+                    return cfail(QQA_ECUDA, "colouring chunk instantiate: %s", cudaGetErrorString(ei));
+                }
+                c->chunk_kernels = k;
+            }
+            COLOR_CK(cudaGraphLaunch(c->chunk_exec, c->st));
+            add_launches((unsigned long long)c->chunk_kernels);
+        } else {
+            const int k = color_enqueue_chunk(c, len, nullptr, c->st);
+            if (k < 0) return k;
+            add_launches((unsigned long long)k);
+        }
+        c->t += len;
+        L -= len;
+    }
     return QQA_OK;
 }
 
@@ -445,7 +612,47 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     c->x = color_alloc<uint8_t>(c, (size_t)n * c->S_pad);
     c->conf = color_alloc<unsigned long long>(c, (size_t)c->S_pad);
     c->nonfinite = color_alloc<unsigned long long>(c, 1);
-    if (!c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] || !c->x || !c->conf ||
+    c->stat = color_alloc<float2>(c, (size_t)n * K);
+    c->rsum = color_alloc<float>(c, (size_t)n * c->S_pad);
+    c->t_dev = color_alloc<int32_t>(c, 1);
+    c->sched = color_alloc<float4>(c, (size_t)prm->steps);
+    // columns per lane of the gather: as many as keep four blocks per SM, else
+    // as many as fit the slab; graphs above 1600 nodes gather directly
+    const int64_t Ccols = (int64_t)K * c->S_pad;
+    const int64_t row_bytes = 128;   // one float per lane
+    for (int vec : {4, 2, 1}) {
+        if (Ccols % (32 * vec) != 0) continue;
+        if ((int64_t)n * row_bytes * vec <= 56 * 1024) {
+            c->gather_vec = vec;
+            break;
+        }
+    }
+    if (!c->gather_vec) {
+        for (int vec : {2, 1}) {
+            if (Ccols % (32 * vec) == 0 && (int64_t)n * row_bytes * vec <= kGatherSlabMax) {
+                c->gather_vec = vec;
+                break;
+            }
+        }
+    }
+    if (c->gather_vec) {
+        c->Y = color_alloc<float>(c, nks);
+        cudaError_t ea = cudaFuncSetAttribute(color_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              kGatherSlabMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(color_gather_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kGatherSlabMax);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(color_gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kGatherSlabMax);
+        if (ea != cudaSuccess) {
+            (void)cudaGetLastError();
+            color_free(c);
+            return cfail(QQA_ECUDA, "cannot raise the shared-memory limit of the gather kernel");
+        }
+    }
+    if (!c->stat || !c->rsum || !c->t_dev || !c->sched || (c->gather_vec && !c->Y) || !c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] ||
+        !c->x || !c->conf ||
         !c->nonfinite) {
         color_free(c);
         return cfail(QQA_ENOMEM, "device allocation for the colouring state failed");
@@ -458,6 +665,23 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sig[0], 0, nks * sizeof(float), c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sig[1], 0, nks * sizeof(float), c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->nonfinite, 0, sizeof(unsigned long long), c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->rsum, 0, sizeof(float) * (size_t)n * c->S_pad, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->stat, 0, sizeof(float2) * (size_t)n * K, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(int32_t), c->st);
+    // per-step scalars: linear gamma schedule (App. C.2), AdamW bias corrections
+    std::vector<float4> sched((size_t)prm->steps);
+    for (int32_t t = 0; t < prm->steps; ++t) {
+        const double gamma = prm->steps > 1 ? (double)prm->gamma_min + ((double)prm->gamma_max - (double)prm->gamma_min) *
+                                                                           (double)t / (double)(prm->steps - 1)
+                                            : (double)prm->gamma_min;
+        const double bc1 = 1.0 - std::pow((double)prm->beta1, (double)(t + 1));
+        const double bc2 = 1.0 - std::pow((double)prm->beta2, (double)(t + 1));
+        sched[t] = make_float4((float)(gamma * (-c->cK * (double)prm->a_ent * (double)K)),
+                               (float)((double)prm->lr / bc1), (float)(1.0 / std::sqrt(bc2)), 0.0f);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->sched, sched.data(), sizeof(float4) * sched.size(), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
         color_free(c);
         return cfail(QQA_ECUDA, "colouring state upload: %s", cudaGetErrorString(e));
@@ -486,10 +710,8 @@ extern "C" int qqa_color_steps(qqa_color *c, int32_t nsteps, int32_t *done)
     if (!c) return cfail(QQA_EINVAL, "colouring handle is NULL");
     if (nsteps < 0) return cfail(QQA_EINVAL, "nsteps must be >= 0");
     const int32_t todo = std::min<int32_t>(nsteps, c->prm.steps - c->t);
-    for (int32_t k = 0; k < todo; ++k) {
-        const int rc = color_launch_step(c, nullptr);
-        if (rc != QQA_OK) return rc;
-    }
+    const int rc = color_run(c, todo);
+    if (rc != QQA_OK) return rc;
     if (done) *done = todo;
     return QQA_OK;
 }
@@ -513,8 +735,10 @@ extern "C" int qqa_color_step_debug(qqa_color *c, float *grad)
         c->grad = color_alloc<float>(c, c->nks());
         if (!c->grad) return cfail(QQA_ENOMEM, "gradient buffer allocation failed");
     }
-    int rc = color_launch_step(c, c->grad);
-    if (rc != QQA_OK) return rc;
+    const int k = color_enqueue_chunk(c, 1, c->grad, c->st);
+    if (k < 0) return k;
+    add_launches((unsigned long long)k);
+    c->t += 1;
     std::vector<float> buf(c->nks());
     COLOR_CK(cudaMemcpyAsync(buf.data(), c->grad, buf.size() * sizeof(float), cudaMemcpyDeviceToHost, c->st));
     COLOR_CK(cudaStreamSynchronize(c->st));
@@ -562,6 +786,9 @@ extern "C" int qqa_color_set_state(qqa_color *c, const float *W, const float *m,
     }
     c->t = t;
     COLOR_CK(cudaMemsetAsync(c->nonfinite, 0, sizeof(unsigned long long), c->st));
+    color_set_t_kernel<<<1, 1, 0, c->st>>>(c->t_dev, t);
+    COLOR_CK(cudaGetLastError());
+    add_launches(1);
     return color_launch_sigma(c, t & 1);
 }
 

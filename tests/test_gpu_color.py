@@ -69,16 +69,37 @@ def test_color_init_is_the_oracle_draw(K, S):
 
 
 @pytest.mark.parametrize("gen,K", [("queens:5:5", 5), ("mycielski:4", 5), ("queens:6:6", 7), ("queens:8:12", 12),
-                                   ("queens:13:13", 13), ("er", 20)])
+                                   ("queens:13:13", 13), ("er", 20), ("er_large", 6)])
 @pytest.mark.parametrize("S", [8, 37, 300])
 def test_color_single_step_matches_oracle(gen, K, S):
-    """Cold moments at t = 0, warm moments at t = 60, with the communication term on."""
-    g = G.erdos_renyi(60, 0.15, 8) if gen == "er" else _graph(gen)
+    """Cold moments at t = 0, warm moments at t = 60, with the communication term on.
+    Graphs of up to 1600 nodes take the shared-memory neighbour sums, the
+    2000-node graph the direct gather."""
+    if gen == "er_large":
+        g = G.erdos_renyi(2000, 0.005, 9)
+    else:
+        g = G.erdos_renyi(60, 0.15, 8) if gen == "er" else _graph(gen)
     p = Params(S=S, steps=400, lr=0.1, alpha_comm=0.3, seed=11, precision=FP32)
     c = qqa.Coloring(g, K, qqa.make_params(p))
     _check_step(g, K, p, c)
     c.steps(59)
     _check_step(g, K, p, c)
+
+
+def test_color_graph_replay_equals_single_launches():
+    """Chunks of steps replayed from a captured CUDA graph (the step index read
+    from the device counter) give the same state, bit for bit, as the same
+    steps launched one at a time, for both the shared-memory and the direct
+    neighbour sums."""
+    for g, K in ((G.queens(6, 6), 7), (G.erdos_renyi(1700, 0.004, 2), 5)):
+        p = Params(S=96, steps=200, lr=0.1, alpha_comm=0.2, seed=4, precision=FP32)
+        a = qqa.Coloring(g, K, qqa.make_params(p))
+        b = qqa.Coloring(g, K, qqa.make_params(p))
+        assert a.steps(70) == 70
+        for _ in range(70):
+            b.steps(1)
+        for x, y in zip(a.get_state(), b.get_state()):
+            np.testing.assert_array_equal(x, y)
 
 
 @pytest.mark.parametrize("a_ent,alpha,T", [(2, 0.0, 1e-3), (4, 1.0, 0.0), (6, 0.5, 1e-3), (8, 0.0, 1e-3)])

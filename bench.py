@@ -123,6 +123,30 @@ def profiled_traffic(workload: str, kernel: str):
     return float(m_b.group(1))
 
 
+def color_source_hash() -> str:
+    """Hash of the sources the colouring kernels are compiled from."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_02135_gb300", "csrc")
+    for name in ("color.cu", "qqa_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def color_profiled_traffic(graph: str):
+    """DRAM bytes of one colouring step (all its kernels, cold cache) from the
+    committed ncu summary, only if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", f"color_step_{graph.replace('-', '_')}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_step:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != color_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -706,6 +730,7 @@ def run_coloring(args):
         total_rs += S * steps * seeds
         total_s += sum(times)
         step_s = dt / steps
+        last_step_s = step_s
         state_bytes = COLOR_BYTES_PER_ELEMENT_STEP * g.n * K * S      # W, m, v read + write, sigma read + write
         gather_bytes = 4 * g.nnz * K * S                               # neighbours' sigma, from L2
         print(json.dumps({"coloring": name, "n": g.n, "edges": g.nnz // 2, "K": K, "S": S, "steps": steps,
@@ -714,10 +739,34 @@ def run_coloring(args):
                           "replica_steps_per_s": S * steps / dt, "us_per_step": step_s * 1e6,
                           "state_GBps": state_bytes / step_s / 1e9, "gather_GBps": gather_bytes / step_s / 1e9,
                           "launches_per_step": launches}), flush=True)
+    # roofline of the step on the largest graph run, and the FP64 oracle beside it
+    name, make, K = chosen[-1]
+    g = make()
+    step_bytes = COLOR_BYTES_PER_ELEMENT_STEP * g.n * K * S
+    achieved = step_bytes / last_step_s / 1e9
+    peak, peak_kind = read_peak()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": color_profiled_traffic(name), "peak_source": peak_kind, "graph": name,
+            "kernel": "colouring step (color_stats + color_gather + color_update)",
+            "algorithmic_bytes_per_step": step_bytes, "us_per_step": last_step_s * 1e6,
+            "note": "working set L2-resident; HBM bandwidth does not bound it"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        p = W.Params(S=S, steps=steps, lr=args.color_lr, seed=0, precision=W.FP32)
+        t0 = time.perf_counter()
+        oracle.color_anneal(g, K, p, steps=2)
+        per = (time.perf_counter() - t0) / 2
+        n_steps = max(2, min(steps, int(args.cpu_seconds / max(per, 1e-9))))
+        t0 = time.perf_counter()
+        oracle.color_anneal(g, K, p, steps=n_steps)
+        dt = time.perf_counter() - t0
+        cpu = {"value": S * n_steps / dt, "unit": "replica-steps/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{name} (n={g.n}, K={K}, S={S}), first {n_steps} of {steps} steps, FP64", "seconds": dt}
     print(json.dumps({"metric": "coloring_replica_steps_per_s", "value": total_rs / total_s,
                       "unit": "replica-steps/s", "graphs": len(chosen), "S": S, "steps": steps,
-                      "seeds": seeds, "dtype": "f32", "data": "synthetic (graphs built from their definitions)"}),
-          flush=True)
+                      "seeds": seeds, "dtype": "f32", "data": "synthetic (graphs built from their definitions)",
+                      "roofline": roof, "cpu_baseline": cpu}), flush=True)
     return 0
 
 

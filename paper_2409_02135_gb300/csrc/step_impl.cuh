@@ -428,7 +428,7 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
     // Langevin noise: all of the lane's replica quads in one lockstep Philox
     // pass when they fit in 16 registers (and the row is held in registers),
     // else one pass per vector
-    constexpr bool kRowNoise = VPL * VEC <= 16 && !Own::kLean;
+    constexpr bool kRowNoise = VPL * VEC <= 16;
     float xi_row[kRowNoise ? VPL : 1][VEC];
     if (kRowNoise) {
         uint32_t qs[VPL * VEC / 4];
@@ -941,8 +941,9 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
 
     // Software pipeline over the warp's tiles: tile records are fetched two
     // tiles ahead, the row bounds and first neighbour indices one tile ahead,
-    // and the slabs one tile ahead, so a tile's only exposed latency is the
-    // gather of its neighbour rows.
+    // the slabs one tile ahead, and the next tile's first neighbour rows are
+    // prefetched into L1 during this tile's update, so little of a tile's
+    // memory latency is exposed.
     const Tile none{0, 0};
     Tile tl_cur = first < num_tiles ? tiles[first] : none;
     Tile tl_nxt = first + W < num_tiles ? tiles[first + W] : none;
@@ -994,6 +995,20 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         if (row < c.n)
             gather_row<T, G, VPL, true>(d, reinterpret_cast<const T *>(d->X[t & 1]), ix, c.S_pad, gl, gmask, Y, dsum,
                                         pol.keep);
+        // the next tile's first neighbour rows (one per lane of the group, up to
+        // G of them) are pulled from L2 into L1 while this tile is updated, so
+        // its gather finds them there; its row bounds and first indices were
+        // requested before this tile's gather
+        if (has_next && ix_cur.k0 + gl < ix_cur.k1) {
+            const InstDesc *__restrict__ dn = descs + tl_cur.slot;
+            const int tn = dn->t + r;
+            if (tn < dn->K) {
+                const char *src = reinterpret_cast<const char *>(reinterpret_cast<const T *>(dn->X[tn & 1]) +
+                                                                 (size_t)ix_cur.jl * dn->S_pad);
+                const int bytes = dn->S_pad * (int)sizeof(T);
+                for (int o = 0; o < bytes; o += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(src + o));
+            }
+        }
         const uint32_t parity = (b ? uses1 : uses0) & 1u;
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[b], parity));
         if (!ok) {

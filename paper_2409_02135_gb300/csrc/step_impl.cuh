@@ -916,8 +916,9 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     }
     __syncwarp();
 
-    // Lane 0 only: start the copies of tile tl's slabs into buffer b (nothing
-    // for a finished instance, whose tile the warp skips). Returns whether it did.
+    // Whole warp: start the copies of tile tl's slabs into buffer b (nothing for
+    // a finished instance, whose tile the warp skips); lanes 0, 1, 2 issue the
+    // copies of p, m and v side by side. Returns whether it did.
     auto issue = [&](const Tile &tl, int b) -> bool {
         const InstDesc *__restrict__ d = descs + tl.slot;
         const int t = d->t + r;
@@ -926,16 +927,22 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         const size_t e0 = (size_t)tl.row0 * d->S_pad;
         const uint32_t pbytes = (uint32_t)(rows * d->S_pad * sizeof(float));
         const uint32_t sbytes = (uint32_t)(rows * d->S_pad * sizeof(T));
-        const float *psrc = d->master ? d->master + e0 : reinterpret_cast<const float *>(d->X[t & 1]) + e0;
-        unsigned char *dst = buf0 + (size_t)b * buf_bytes;
-        const size_t mofs = (size_t)R * d->S_pad * sizeof(float);
-        const size_t vofs = mofs + (size_t)R * d->S_pad * sizeof(T);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&mbar[b], pbytes + 2 * sbytes);
-        // (FP32 runs read p^t itself here; it is gathered too, so it is kept)
-        tma_bulk_load_hint(dst, psrc, pbytes, &mbar[b], d->master ? pol.stream : pol.keep);
-        tma_bulk_load_hint(dst + mofs, reinterpret_cast<const T *>(d->m) + e0, sbytes, &mbar[b], pol.stream);
-        tma_bulk_load_hint(dst + vofs, reinterpret_cast<const T *>(d->v) + e0, sbytes, &mbar[b], pol.stream);
+        if (lane == 0) mbar_arrive_expect_tx(&mbar[b], pbytes + 2 * sbytes);
+        __syncwarp();   // the expected bytes are registered before any copy can land
+        if (lane < 3) {
+            const size_t mofs = (size_t)R * d->S_pad * sizeof(float);
+            const size_t vofs = mofs + (size_t)R * d->S_pad * sizeof(T);
+            unsigned char *dst = buf0 + (size_t)b * buf_bytes + (lane == 0 ? 0 : (lane == 1 ? mofs : vofs));
+            const void *src;
+            if (lane == 0)
+                src = d->master ? d->master + e0 : reinterpret_cast<const float *>(d->X[t & 1]) + e0;
+            else
+                src = reinterpret_cast<const T *>(lane == 1 ? d->m : d->v) + e0;
+            // (FP32 runs read p^t itself here; it is gathered too, so it is kept)
+            const uint64_t hint = (lane == 0 && !d->master) ? pol.keep : pol.stream;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_bulk_load_hint(dst, src, lane == 0 ? pbytes : sbytes, &mbar[b], hint);
+        }
         return true;
     };
 
@@ -949,8 +956,8 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     Tile tl_nxt = first + W < num_tiles ? tiles[first + W] : none;
     RowIdx ix_cur = first < num_tiles ? load_row_idx(descs + tl_cur.slot, tl_cur.row0 + grp, gl) : RowIdx{0, 0, 0, 0.0f};
 
-    // completed phases of each buffer's barrier (warp-uniform), and lane 0's
-    // record of a copy in flight into the buffer not being read
+    // completed phases of each buffer's barrier, and whether a copy is in
+    // flight into the buffer not being read (warp-uniform)
     uint32_t uses0 = 0u, uses1 = 0u;
     bool next_pending = false;
     int b = 0;
@@ -958,11 +965,11 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     // tiles of a warp belong to the same instance)
     int ctx_slot = -1;
     StepCtx c{};
-    if (lane == 0 && first < num_tiles) issue(tl_cur, 0);
+    if (first < num_tiles) issue(tl_cur, 0);
     for (int tile = first; tile < num_tiles; tile += W, b ^= 1) {
         const bool has_next = tile + W < num_tiles;
         // buffer b^1 was last read in the previous iteration, which ended in __syncwarp
-        if (lane == 0) next_pending = has_next && issue(tl_nxt, b ^ 1);
+        next_pending = has_next && issue(tl_nxt, b ^ 1);
         RowIdx ix_nxt{0, 0, 0, 0.0f};
         if (has_next) ix_nxt = load_row_idx(descs + tl_nxt.slot, tl_nxt.row0 + grp, gl);
         const Tile tl_nn = tile + 2 * W < num_tiles ? tiles[tile + 2 * W] : none;

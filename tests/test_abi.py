@@ -93,3 +93,37 @@ def test_request_bytes_accounting(lib):
     bf16 = qqa.request_bytes(n, nnz, S, qqa.BF16, weighted=True)
     elems16 = n * 104
     assert bf16 == elems16 * 12 + n * 4 * 4 + 104 * 56 + 32 * 4 + 4096 + 4 * (n + 1) + 8 * nnz
+
+
+def _color_create(lib, n, rp, col, K, **kw):
+    from paper_2409_02135_gb300._lib import qqa_params
+    p = qqa_params()
+    lib.qqa_default_params(ctypes.byref(p))
+    p.S, p.steps = 8, 10
+    for k, v in kw.items():
+        setattr(p, k, v)
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col if col else [0], dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    h = ctypes.c_void_p()
+    rc = lib.qqa_color_create(n, rp.ctypes.data_as(P), col.ctypes.data_as(P), K, ctypes.byref(p), None,
+                              ctypes.byref(h))
+    return rc, lib.qqa_last_error().decode()
+
+
+@pytest.mark.parametrize("case,rp,col,K,kw,msg", [
+    ("one colour", [0, 1, 2], [1, 0], 1, {}, "K must be"),
+    ("too many colours", [0, 1, 2], [1, 0], 33, {}, "K must be"),
+    ("no replicas", [0, 1, 2], [1, 0], 3, {"S": 0}, "S must be"),
+    ("no steps", [0, 1, 2], [1, 0], 3, {"steps": 0}, "steps must be"),
+    ("odd entropy exponent", [0, 1, 2], [1, 0], 3, {"a_ent": 3}, "a_ent"),
+    ("BF16", [0, 1, 2], [1, 0], 3, {"precision": 1}, "FP32"),
+    ("asymmetric", [0, 1, 1], [1], 3, {}, "reverse"),
+    ("self-loop", [0, 1, 1], [0], 3, {}, "self-loop"),
+])
+def test_color_create_rejects_bad_arguments(lib, case, rp, col, K, kw, msg):
+    """qqa_color_create checks its arguments and the graph on the host, before
+    any device work."""
+    rc, err = _color_create(lib, len(rp) - 1, rp, col, K, **kw)
+    assert rc == -1, case
+    assert msg in err, (case, err)

@@ -7,7 +7,7 @@
 // [0,1]). Rows of one (i, k) are S_pad = S rounded up to 32 floats long, so a
 // warp reads 128 contiguous bytes of one colour plane.
 //
-// One step is two launches:
+// One step is two launches (one for graphs above 1600 nodes):
 //   color_gather_kernel  Y = A sigma, the neighbour sums of the relaxed
 //                        conflicts, as a sparse-times-dense product over the
 //                        columns (k, s) of sigma staged in shared memory
@@ -83,34 +83,52 @@ struct ColorStepArgs {
     uint32_t seed_lo, seed_hi;
 };
 
-// Replica statistics of sigma for the communication term (Eq. 10), one warp
-// per (node, colour) row: mean over the S replicas, then the population
-// variance as the mean of squared deviations (two passes; the second reads
-// the row from L1). stat[r] = (mean, -alpha / sqrt(var + eps)).
-__global__ void __launch_bounds__(256) color_stats_kernel(int32_t rows, int32_t S, int32_t S_pad, float alpha,
-                                                          float comm_eps, const float *__restrict__ sig0,
-                                                          const float *__restrict__ sig1,
-                                                          const int32_t *__restrict__ t_dev, int32_t step_off,
-                                                          float2 *__restrict__ stat)
+// Replica statistics of sigma for the communication term (Eq. 10) are carried
+// from step to step as per-chunk partial sums: for every (node i, colour k)
+// and chunk c of 128 replicas, part[c] = (sum d, sum d^2) with d = sigma - h
+// and the shift h = the mean of the previous step's sigma, so the one-pass
+// variance sum d^2 / S - (sum d / S)^2 has no cancellation to speak of. The
+// update kernel of a step combines the partials of its sigma and writes those
+// of the next sigma; both are double-buffered by step parity.
+constexpr int kMaxChunks = 8;   // chunks of 128 replicas (S <= 1024)
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Partials of the sigma in buffer `sig` (a state set from the host, or the
+// initial draw), one warp per (node, colour) row: the mean first (two passes),
+// then the partials of every chunk about it.
+__global__ void __launch_bounds__(256) color_stats_init_kernel(int32_t rows, int32_t S, int32_t S_pad,
+                                                               const float *__restrict__ sig,
+                                                               float2 *__restrict__ part, float *__restrict__ shift)
 {
     const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
-    const float *__restrict__ sig = ((*t_dev + step_off) & 1) ? sig1 : sig0;
     const float *row = sig + (size_t)r * S_pad;
     float acc = 0.0f;
     for (int s = lane; s < S; s += 32) acc += row[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    const float mean = acc / (float)S;
-    float ss = 0.0f;
-    for (int s = lane; s < S; s += 32) {
-        const float d = row[s] - mean;
-        ss = fmaf(d, d, ss);
+    const float mean = warp_sum(acc) / (float)S;
+    const int chunks = (S_pad / 4 + 31) / 32;
+    for (int c = 0; c < chunks; ++c) {
+        float sd = 0.0f, sd2 = 0.0f;
+        for (int e = 0; e < 4; ++e) {
+            const int s = 128 * c + 4 * lane + e;
+            if (s < S) {
+                const float d = row[s] - mean;
+                sd += d;
+                sd2 = fmaf(d, d, sd2);
+            }
+        }
+        sd = warp_sum(sd);
+        sd2 = warp_sum(sd2);
+        if (lane == 0) part[(size_t)r * kMaxChunks + c] = make_float2(sd, sd2);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) stat[r] = make_float2(mean, -alpha / sqrtf(fmaf(ss, 1.0f / (float)S, comm_eps)));
+    if (lane == 0) shift[r] = mean;
 }
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -123,13 +141,17 @@ __device__ __forceinline__ void st4(float *p, const float (&v)[4])
 // c = blockIdx.x % chunks: warp k of the block (K warps) owns colour k, so
 // every access is a coalesced 16-byte-per-lane row of one (i, k) plane. The
 // sums over colours (sum_k sigma_k g_k of the chain rule, sum_k W'_k of the
-// next relaxation) meet in shared memory. stat[i*K + k] = (mean, -alpha /
-// STD) of this step (unused when alpha = 0); rsum[i][s] holds sum_k W of this
-// step on entry and of the next on exit. Ygat is NULL for graphs too large
-// for color_gather_kernel: the neighbour sums are then gathered here.
-__global__ void __launch_bounds__(1024)
+// next relaxation) meet in shared memory. With alpha != 0 the replica
+// statistics of this step come from the partials (part, shift) of its parity,
+// and the block writes those of the next sigma for its chunk; rsum[i][s]
+// holds sum_k W of this step on entry and of the next on exit. Ygat is NULL
+// for graphs too large for color_gather_kernel: the neighbour sums are then
+// gathered here.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT)
 color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                    const float2 *__restrict__ stat, const float *__restrict__ Ygat, float *__restrict__ sig0,
+                    float2 *__restrict__ part, float *__restrict__ shift, const float *__restrict__ Ygat,
+                    float *__restrict__ sig0,
                     float *__restrict__ sig1, float *__restrict__ W, float *__restrict__ M,
                     float *__restrict__ V, float *__restrict__ rsum, float *__restrict__ grad_dbg,
                     unsigned long long *__restrict__ nonfinite)
@@ -142,11 +164,30 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
     const int K = a.K;
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = (int)(blockIdx.x / (unsigned)chunks);
-    const int q = (int)(blockIdx.x % (unsigned)chunks) * 32 + lane, s0 = 4 * q;
+    const int chunk = (int)(blockIdx.x % (unsigned)chunks);
+    const int q = chunk * 32 + lane, s0 = 4 * q;
     const bool live = s0 < a.S;
     const size_t plane = (size_t)a.S_pad, node = (size_t)K * plane;
     const size_t idx = (size_t)i * node + (size_t)k * plane + s0;
     const float fK = (float)K;
+    const bool comm = a.alpha != 0.0f;
+    const size_t ik = (size_t)i * K + k, nk = (size_t)a.n * K;
+    // mean and -alpha / STD of sigma_ik over the replicas (Eq. 10), from the partials
+    float mean = 0.0f, coef = 0.0f;
+    if (comm && k < K) {
+        const float2 *__restrict__ pc = part + (size_t)(t & 1) * nk * kMaxChunks + ik * kMaxChunks;
+        float sd = 0.0f, sd2 = 0.0f;
+        for (int c = 0; c < chunks; ++c) {
+            const float2 pv = pc[c];
+            sd += pv.x;
+            sd2 += pv.y;
+        }
+        const float inv_S = 1.0f / (float)a.S;
+        const float md = sd * inv_S;
+        mean = shift[(size_t)(t & 1) * nk + ik] + md;
+        const float var = fmaxf(fmaf(sd2, inv_S, -md * md), 0.0f);
+        coef = -a.alpha / sqrtf(var + a.comm_eps);
+    }
 
     float g[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (live) {
@@ -163,8 +204,6 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
         }
         const float4 sv = ld4(sig_cur + idx);
         sg[0] = sv.x, sg[1] = sv.y, sg[2] = sv.z, sg[3] = sv.w;
-        float2 st = make_float2(0.0f, 0.0f);
-        if (a.alpha != 0.0f) st = stat[(size_t)i * K + k];
         // dR/dsigma: + entropy s_K + communication
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -172,7 +211,7 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
             const float u2 = u * u;
             float upow = u;
             for (int h = 0; h < a.half_pow; ++h) upow *= u2;
-            g[e] = fmaf(st.y, sg[e] - st.x, fmaf(sc.x, upow, g[e]));
+            g[e] = fmaf(coef, sg[e] - mean, fmaf(sc.x, upow, g[e]));
         }
     }
     xk[k][lane] = make_float4(sg[0] * g[0], sg[1] * g[1], sg[2] * g[2], sg[3] * g[3]);
@@ -219,6 +258,7 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
         const float4 d = xk[kk][lane];
         ns[0] += d.x, ns[1] += d.y, ns[2] += d.z, ns[3] += d.w;
     }
+    float sd = 0.0f, sd2 = 0.0f;
     if (live) {
         // sigma' = W' / sum_k W' (1/K for a zero row), and the row sums
         float sp[4];
@@ -226,6 +266,22 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
         for (int e = 0; e < 4; ++e) sp[e] = ns[e] > 0.0f ? wn[e] * (1.0f / ns[e]) : 1.0f / fK;
         st4(sig_next + idx, sp);
         if (k == 0) st4(rsum + (size_t)i * plane + s0, ns);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (s0 + e < a.S) {
+                const float d = sp[e] - mean;   // about this step's mean, the next step's shift
+                sd += d;
+                sd2 = fmaf(d, d, sd2);
+            }
+    }
+    if (comm) {   // partials of the next sigma for this chunk (whole warps)
+        sd = warp_sum(sd);
+        sd2 = warp_sum(sd2);
+        if (lane == 0) {
+            const int tn = (t + 1) & 1;
+            part[(size_t)tn * nk * kMaxChunks + ik * kMaxChunks + chunk] = make_float2(sd, sd2);
+            if (chunk == 0) shift[(size_t)tn * nk + ik] = mean;
+        }
     }
 }
 
@@ -402,7 +458,8 @@ struct qqa_color {
     int sms = 0;
     int32_t *rp = nullptr, *col = nullptr;
     float *W = nullptr, *m = nullptr, *v = nullptr, *sig[2] = {nullptr, nullptr}, *grad = nullptr;
-    float2 *stat = nullptr;   // (mean, -alpha / STD) per (node, colour)
+    float2 *part = nullptr;   // [2][n][K][kMaxChunks] partial replica sums of sigma
+    float *shift = nullptr;   // [2][n][K] their shifts
     float *rsum = nullptr;    // sum_k W per (node, replica)
     float *Y = nullptr;       // neighbour sums when the graph fits color_gather_kernel's slab
     int gather_vec = 0;       // 4, 2 or 1: columns per lane of color_gather_kernel; 0: direct gather
@@ -441,14 +498,18 @@ static T *color_alloc(qqa_color *c, size_t count)
     return (T *)p;
 }
 
-// sigma and the row sums of the current W into buffer `which`.
+// sigma and the row sums of the current W into buffer `which`, and the
+// partial replica sums of that sigma.
 static int color_launch_sigma(qqa_color *c, int which)
 {
     const int64_t total = (int64_t)c->n * c->S_pad;
     color_sigma_kernel<<<(unsigned)((total + 255) / 256), 256, 0, c->st>>>(c->n, c->K, c->S, c->S_pad, c->W,
                                                                         c->sig[which], c->rsum);
+    const int rows = c->n * c->K;
+    color_stats_init_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, c->st>>>(
+        rows, c->S, c->S_pad, c->sig[which], c->part + (size_t)which * rows * kMaxChunks, c->shift + (size_t)which * rows);
     COLOR_CK(cudaGetLastError());
-    add_launches(1);
+    add_launches(2);
     return QQA_OK;
 }
 
@@ -481,13 +542,6 @@ static int color_enqueue_chunk(qqa_color *c, int L, float *grad_dbg, cudaStream_
     int kernels = 0;
     for (int r = 0; r < L; ++r) {
         a.r = r;
-        if (p.alpha_comm != 0.0f) {
-            const int rows = c->n * c->K;
-            color_stats_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(rows, c->S, c->S_pad, p.alpha_comm,
-                                                                          p.comm_eps, c->sig[0], c->sig[1], c->t_dev,
-                                                                          r, c->stat);
-            ++kernels;
-        }
         const float *Ygat = nullptr;
         if (c->gather_vec) {
             const int vec = c->gather_vec;
@@ -512,8 +566,9 @@ static int color_enqueue_chunk(qqa_color *c, int L, float *grad_dbg, cudaStream_
             Ygat = c->Y;
         }
         const int chunks = (c->S_pad / 4 + 31) / 32;   // 32 quads of replicas per block
-        color_update_kernel<<<(unsigned)((int64_t)c->n * chunks), 32 * c->K, 0, st>>>(
-            a, chunks, c->rp, c->col, c->stat, Ygat, c->sig[0], c->sig[1], c->W, c->m, c->v, c->rsum, grad_dbg,
+        auto update = c->K <= 16 ? color_update_kernel<512> : color_update_kernel<1024>;
+        update<<<(unsigned)((int64_t)c->n * chunks), 32 * c->K, 0, st>>>(
+            a, chunks, c->rp, c->col, c->part, c->shift, Ygat, c->sig[0], c->sig[1], c->W, c->m, c->v, c->rsum, grad_dbg,
             c->nonfinite);
         ++kernels;
     }
@@ -612,7 +667,8 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     c->x = color_alloc<uint8_t>(c, (size_t)n * c->S_pad);
     c->conf = color_alloc<unsigned long long>(c, (size_t)c->S_pad);
     c->nonfinite = color_alloc<unsigned long long>(c, 1);
-    c->stat = color_alloc<float2>(c, (size_t)n * K);
+    c->part = color_alloc<float2>(c, (size_t)2 * n * K * kMaxChunks);
+    c->shift = color_alloc<float>(c, (size_t)2 * n * K);
     c->rsum = color_alloc<float>(c, (size_t)n * c->S_pad);
     c->t_dev = color_alloc<int32_t>(c, 1);
     c->sched = color_alloc<float4>(c, (size_t)prm->steps);
@@ -651,7 +707,7 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
             return cfail(QQA_ECUDA, "cannot raise the shared-memory limit of the gather kernel");
         }
     }
-    if (!c->stat || !c->rsum || !c->t_dev || !c->sched || (c->gather_vec && !c->Y) || !c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] ||
+    if (!c->part || !c->shift || !c->rsum || !c->t_dev || !c->sched || (c->gather_vec && !c->Y) || !c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] ||
         !c->x || !c->conf ||
         !c->nonfinite) {
         color_free(c);
@@ -666,7 +722,8 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     if (e == cudaSuccess) e = cudaMemsetAsync(c->sig[1], 0, nks * sizeof(float), c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->nonfinite, 0, sizeof(unsigned long long), c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->rsum, 0, sizeof(float) * (size_t)n * c->S_pad, c->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->stat, 0, sizeof(float2) * (size_t)n * K, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->part, 0, sizeof(float2) * (size_t)2 * n * K * kMaxChunks, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->shift, 0, sizeof(float) * (size_t)2 * n * K, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(int32_t), c->st);
     // per-step scalars: linear gamma schedule (App. C.2), AdamW bias corrections
     std::vector<float4> sched((size_t)prm->steps);

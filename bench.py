@@ -747,7 +747,7 @@ def run_coloring(args):
     peak, peak_kind = read_peak()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": color_profiled_traffic(name), "peak_source": peak_kind, "graph": name,
-            "kernel": "colouring step (color_gather + color_update)",
+            "kernel": "colouring step (neighbour sums + color_update)",
             "algorithmic_bytes_per_step": step_bytes, "us_per_step": last_step_s * 1e6,
             "note": "working set L2-resident; HBM bandwidth does not bound it"}
     cpu = None

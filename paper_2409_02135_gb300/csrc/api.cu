@@ -594,6 +594,26 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
+// A 2-D fp16 tensor map with 128-byte swizzle (shared with color.cu): `outer`
+// rows of `inner` elements, rows `row_bytes` apart, box of box_inner x
+// box_outer. Returns 0 on success.
+namespace qqa {
+int encode_tmap_f16_2d(void *map_out, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                       uint32_t box_inner, uint32_t box_outer)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return -1;
+    const cuuint32_t es[2] = {1, 1};
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer}, str[1] = {(cuuint64_t)row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const CUresult cr = enc(reinterpret_cast<CUtensorMap *>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                            const_cast<void *>(base), dims, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return cr == CUDA_SUCCESS ? 0 : (int)cr;
+}
+}  // namespace qqa
+
 // Adjacency in fp16, state planes, and the five TMA tensor maps of a dense slot.
 static int setup_dense_slot(qqa_run *r, int32_t k, InstDesc &d, std::vector<void *> &dev, cudaStream_t st)
 {

@@ -39,10 +39,15 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda.h>
+#include <cuda_fp16.h>
+
 #include "../../include/qqa.h"
 #include "qqa_internal.cuh"
 
 namespace qqa {
+int encode_tmap_f16_2d(void *map_out, const void *base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                       uint32_t box_inner, uint32_t box_outer);
 int set_error(int code, const char *msg);
 int check_unit_graph(int32_t n, const int32_t *rp, const int32_t *col);
 void add_launches(unsigned long long k);
@@ -363,6 +368,227 @@ __global__ void __launch_bounds__(256) color_gather_kernel(int32_t n, int64_t C,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Neighbour sums on the tensor cores, for dense graphs of up to 4096 nodes:
+// Y = A sigma with A the 0/1 adjacency in fp16 [n_pad][n_pad] (exact) and
+// sigma in two fp16 planes stored transposed, [C][n_pad] (C = K * S_pad):
+// hi = fp16(sigma) and lo = fp16((sigma - hi) * 2^12). hi + lo 2^-12 carries
+// about 22 significant bits; the scale keeps lo a normal fp16 number for every
+// sigma in [0, 1]. The two products accumulate in separate FP32 tensor-memory
+// accumulators (every product is exact) and Y = D_hi + 2^-12 D_lo.
+// ---------------------------------------------------------------------------
+constexpr int kTcMinNodes = 112, kTcMaxNodes = 4096;
+constexpr double kTcMinDensity = 0.05;   // nnz / n^2 below which the dense product wastes the tensor cores
+
+// sigma [n][C] -> hi, lo planes [C][n_pad], through a 64 x 32 shared tile
+__global__ void __launch_bounds__(256) color_planes_kernel(int32_t n, int32_t n_pad, int32_t C,
+                                                           const float *__restrict__ sig0,
+                                                           const float *__restrict__ sig1,
+                                                           const int32_t *__restrict__ t_dev, int32_t step_off,
+                                                           __half *__restrict__ hi, __half *__restrict__ lo)
+{
+    __shared__ float tile[64][33];
+    const float *__restrict__ sig = ((*t_dev + step_off) & 1) ? sig1 : sig0;
+    const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
+    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+        const int r = e >> 6, cc = e & 63;
+        const int i = i0 + r, c = c0 + cc;
+        tile[cc][r] = (i < n && c < C) ? sig[(size_t)i * C + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+        const int cc = e >> 5, r = e & 31;
+        const int i = i0 + r, c = c0 + cc;
+        if (i < n && c < C) {
+            const float x = tile[cc][r];
+            const __half h = __float2half_rn(x);
+            hi[(size_t)c * n_pad + i] = h;
+            lo[(size_t)c * n_pad + i] = __float2half_rn((x - __half2float(h)) * 4096.0f);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr)
+{
+    // K-major operand with 128-byte swizzle: start address >> 4, leading byte
+    // offset 1 (unused by this layout), stride byte offset 1024 >> 4 (eight
+    // 128-byte rows), descriptor version 1, layout 2 (128-byte swizzle)
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)64 << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tc_tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Wait for phase `parity` of an mbarrier, for about a second at most.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    const long long start = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - start > (1LL << 31)) return false;
+    }
+}
+
+constexpr int kTcStages = 2;
+constexpr int kTcThreads = 160;   // 4 epilogue warps (TMEM lanes 0..127) + 1 control warp
+
+__host__ __device__ constexpr int tc_stage_bytes(int NT) { return 128 * 128 + 2 * NT * 128; }
+__host__ __device__ constexpr int tc_smem_bytes(int NT) { return 1024 + kTcStages * tc_stage_bytes(NT) + 64; }
+
+// One CTA per (128-row tile m, NT-column tile c): D_hi, D_lo = A[m rows] . {hi, lo}[c cols]^T
+// over K = n_pad in 64-wide chunks (TMA, two stages, bounded waits), then
+// Y[row][c0 + col] = D_hi + 2^-12 D_lo for the tile's rows below n.
+// tmaps: A, hi, lo (device copies of CUtensorMap).
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads, 1)
+color_gather_tc_kernel(int32_t n, int32_t n_pad, int64_t C, const void *__restrict__ tmaps, float *__restrict__ Y,
+                       unsigned long long *__restrict__ timeouts)
+{
+    constexpr int A_BYTES = 128 * 128, B_BYTES = NT * 128, STAGE = tc_stage_bytes(NT);
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *mb_full = reinterpret_cast<uint64_t *>(base + kTcStages * STAGE);
+    uint64_t *mb_empty = mb_full + kTcStages;
+    uint64_t *mb_acc = mb_empty + kTcStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mb_acc + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * 128;
+    const int c0 = blockIdx.y * NT;
+    const int nK = n_pad / 64;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kTcStages; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_full + k)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_empty + k)) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mb_acc)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "n"(2 * NT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    if (warp == 4) {
+        if (lane == 0) {
+            const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(tmaps);
+            const CUtensorMap *tmA = tm, *tmH = tm + 1, *tmL = tm + 2;
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmH) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmL) : "memory");
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+            auto fill = [&](int kc) {
+                const int st = kc % kTcStages;
+                if (kc >= kTcStages) ok = ok && tc_wait(smem_addr(mb_empty + st), ((kc / kTcStages) - 1) & 1);
+                if (!ok) return;
+                unsigned char *sp = base + st * STAGE;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb_full + st)),
+                             "r"(STAGE)
+                             : "memory");
+                tc_tma_load_2d(smem_addr(sp), tmA, 64 * kc, row0, smem_addr(mb_full + st));
+                tc_tma_load_2d(smem_addr(sp + A_BYTES), tmH, 64 * kc, c0, smem_addr(mb_full + st));
+                tc_tma_load_2d(smem_addr(sp + A_BYTES + B_BYTES), tmL, 64 * kc, c0, smem_addr(mb_full + st));
+            };
+            for (int kc = 0; kc < kTcStages && kc < nK; ++kc) fill(kc);
+            for (int kc = 0; kc < nK && ok; ++kc) {
+                const int st = kc % kTcStages;
+                ok = tc_wait(smem_addr(mb_full + st), (kc / kTcStages) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_addr(base + st * STAGE);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint64_t ad = tc_desc_sw128(sa + ks * 32);
+                    const uint64_t bh = tc_desc_sw128(sa + A_BYTES + ks * 32);
+                    const uint64_t bl = tc_desc_sw128(sa + A_BYTES + B_BYTES + ks * 32);
+                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    tc_mma_f16(tmem, ad, bh, idesc, acc);
+                    tc_mma_f16(tmem + NT, ad, bl, idesc, acc);
+                }
+                tc_commit(smem_addr(mb_empty + st));   // stage free once these MMAs are done
+                if (kc + kTcStages < nK) fill(kc + kTcStages);
+            }
+            if (ok) tc_commit(smem_addr(mb_acc));
+            else atomicAdd(timeouts, 1ULL);
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps: TMEM lane = row of the tile
+        const bool acc_ok = tc_wait(smem_addr(mb_acc), 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!acc_ok) {
+            if (threadIdx.x == 0) atomicAdd(timeouts, 1ULL);
+        } else {
+            const int row = row0 + 32 * warp + lane;
+            float *__restrict__ yrow = Y + (size_t)row * C + c0;
+#pragma unroll 1
+            for (int c16 = 0; c16 < NT; c16 += 16) {
+                uint32_t vh[16], vl[16];
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c16, vh);
+                tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(NT + c16), vl);
+                if (row < n) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4 *>(yrow + c16 + e) =
+                            make_float4(fmaf(__uint_as_float(vl[e]), 2.44140625e-4f, __uint_as_float(vh[e])),
+                                        fmaf(__uint_as_float(vl[e + 1]), 2.44140625e-4f, __uint_as_float(vh[e + 1])),
+                                        fmaf(__uint_as_float(vl[e + 2]), 2.44140625e-4f, __uint_as_float(vh[e + 2])),
+                                        fmaf(__uint_as_float(vl[e + 3]), 2.44140625e-4f, __uint_as_float(vh[e + 3])));
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(2 * NT) : "memory");
+    }
+}
+
 // The step counter of the device: advanced after each chunk, set from the host.
 __global__ void color_advance_kernel(int32_t *t_dev, int32_t by) { *t_dev += by; }
 __global__ void color_set_t_kernel(int32_t *t_dev, int32_t t) { *t_dev = t; }
@@ -463,6 +689,11 @@ struct qqa_color {
     float *rsum = nullptr;    // sum_k W per (node, replica)
     float *Y = nullptr;       // neighbour sums when the graph fits color_gather_kernel's slab
     int gather_vec = 0;       // 4, 2 or 1: columns per lane of color_gather_kernel; 0: direct gather
+    int tc_nt = 0;            // > 0: neighbour sums on the tensor cores, NT columns per CTA
+    int n_pad = 0;            // n rounded up to 128 (tensor-core path)
+    __half *A16 = nullptr, *hi = nullptr, *lo = nullptr;   // fp16 adjacency and sigma planes
+    void *tmaps = nullptr;    // tensor maps of A16, hi, lo
+    unsigned long long *timeouts = nullptr;
     int32_t *t_dev = nullptr; // step counter of the device
     float4 *sched = nullptr;  // per-step scalars, [steps]
     uint8_t *x = nullptr;
@@ -543,7 +774,20 @@ static int color_enqueue_chunk(qqa_color *c, int L, float *grad_dbg, cudaStream_
     for (int r = 0; r < L; ++r) {
         a.r = r;
         const float *Ygat = nullptr;
-        if (c->gather_vec) {
+        if (c->tc_nt) {
+            const int C = c->K * c->S_pad;
+            color_planes_kernel<<<dim3((unsigned)((c->n + 31) / 32), (unsigned)((C + 63) / 64)), 256, 0, st>>>(
+                c->n, c->n_pad, C, c->sig[0], c->sig[1], c->t_dev, r, c->hi, c->lo);
+            const dim3 grid((unsigned)(c->n_pad / 128), (unsigned)(C / c->tc_nt));
+            if (c->tc_nt == 128)
+                color_gather_tc_kernel<128><<<grid, kTcThreads, tc_smem_bytes(128), st>>>(c->n, c->n_pad, C, c->tmaps,
+                                                                                        c->Y, c->timeouts);
+            else
+                color_gather_tc_kernel<64><<<grid, kTcThreads, tc_smem_bytes(64), st>>>(c->n, c->n_pad, C, c->tmaps,
+                                                                                      c->Y, c->timeouts);
+            kernels += 2;
+            Ygat = c->Y;
+        } else if (c->gather_vec) {
             const int vec = c->gather_vec;
             const int64_t C = (int64_t)c->K * c->S_pad;
             const int smem = c->n * 128 * vec;
@@ -671,6 +915,7 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     c->shift = color_alloc<float>(c, (size_t)2 * n * K);
     c->rsum = color_alloc<float>(c, (size_t)n * c->S_pad);
     c->t_dev = color_alloc<int32_t>(c, 1);
+    c->timeouts = color_alloc<unsigned long long>(c, 1);
     c->sched = color_alloc<float4>(c, (size_t)prm->steps);
     // columns per lane of the gather: as many as keep four blocks per SM, else
     // as many as fit the slab; graphs above 1600 nodes gather directly
@@ -691,6 +936,51 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
             }
         }
     }
+    {
+        const double density = (double)c->nnz / ((double)n * (double)n);
+        if (n >= kTcMinNodes && n <= kTcMaxNodes && density >= kTcMinDensity && Ccols % 64 == 0)
+            c->tc_nt = Ccols % 128 == 0 ? 128 : 64;
+    }
+    if (c->tc_nt) {
+        c->gather_vec = 0;
+        c->n_pad = (n + 127) / 128 * 128;
+        c->A16 = color_alloc<__half>(c, (size_t)c->n_pad * c->n_pad);
+        c->hi = color_alloc<__half>(c, (size_t)Ccols * c->n_pad);
+        c->lo = color_alloc<__half>(c, (size_t)Ccols * c->n_pad);
+        c->tmaps = color_alloc<unsigned char>(c, 3 * sizeof(CUtensorMap));
+        c->Y = color_alloc<float>(c, nks);
+        if (!c->A16 || !c->hi || !c->lo || !c->tmaps || !c->Y) {
+            color_free(c);
+            return cfail(QQA_ENOMEM, "device allocation for the tensor-core neighbour sums failed");
+        }
+        alignas(64) CUtensorMap maps[3];
+        const uint64_t rb = (uint64_t)c->n_pad * 2;
+        int er = encode_tmap_f16_2d(&maps[0], c->A16, (uint64_t)c->n_pad, (uint64_t)c->n_pad, rb, 64, 128);
+        if (!er) er = encode_tmap_f16_2d(&maps[1], c->hi, (uint64_t)c->n_pad, (uint64_t)Ccols, rb, 64, (uint32_t)c->tc_nt);
+        if (!er) er = encode_tmap_f16_2d(&maps[2], c->lo, (uint64_t)c->n_pad, (uint64_t)Ccols, rb, 64, (uint32_t)c->tc_nt);
+        if (er) {
+            color_free(c);
+            return cfail(QQA_ECUDA, "tensor map encoding failed (%d)", er);
+        }
+        std::vector<uint16_t> a16((size_t)c->n_pad * c->n_pad, 0);
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) a16[(size_t)i * c->n_pad + col[e]] = 0x3C00u;   // fp16 1.0
+        cudaError_t ea = cudaMemcpy(c->A16, a16.data(), a16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (ea == cudaSuccess) ea = cudaMemcpy(c->tmaps, maps, sizeof maps, cudaMemcpyHostToDevice);
+        if (ea == cudaSuccess) ea = cudaMemset(c->hi, 0, (size_t)Ccols * c->n_pad * sizeof(__half));
+        if (ea == cudaSuccess) ea = cudaMemset(c->lo, 0, (size_t)Ccols * c->n_pad * sizeof(__half));
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(color_gather_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_smem_bytes(128));
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute(color_gather_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tc_smem_bytes(64));
+        if (ea != cudaSuccess) {
+            (void)cudaGetLastError();
+            color_free(c);
+            return cfail(QQA_ECUDA, "tensor-core neighbour sums setup: %s", cudaGetErrorString(ea));
+        }
+    }
     if (c->gather_vec) {
         c->Y = color_alloc<float>(c, nks);
         cudaError_t ea = cudaFuncSetAttribute(color_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -707,7 +997,7 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
             return cfail(QQA_ECUDA, "cannot raise the shared-memory limit of the gather kernel");
         }
     }
-    if (!c->part || !c->shift || !c->rsum || !c->t_dev || !c->sched || (c->gather_vec && !c->Y) || !c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] ||
+    if (!c->part || !c->shift || !c->rsum || !c->t_dev || !c->timeouts || !c->sched || (c->gather_vec && !c->Y) || !c->rp || !c->col || !c->W || !c->m || !c->v || !c->sig[0] || !c->sig[1] ||
         !c->x || !c->conf ||
         !c->nonfinite) {
         color_free(c);
@@ -725,6 +1015,7 @@ extern "C" int qqa_color_create(int32_t n, const int32_t *row_ptr, const int32_t
     if (e == cudaSuccess) e = cudaMemsetAsync(c->part, 0, sizeof(float2) * (size_t)2 * n * K * kMaxChunks, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->shift, 0, sizeof(float) * (size_t)2 * n * K, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->t_dev, 0, sizeof(int32_t), c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->timeouts, 0, sizeof(unsigned long long), c->st);
     // per-step scalars: linear gamma schedule (App. C.2), AdamW bias corrections
     std::vector<float4> sched((size_t)prm->steps);
     for (int32_t t = 0; t < prm->steps; ++t) {
@@ -776,9 +1067,11 @@ extern "C" int qqa_color_steps(qqa_color *c, int32_t nsteps, int32_t *done)
 extern "C" int qqa_color_sync(qqa_color *c)
 {
     if (!c) return cfail(QQA_EINVAL, "colouring handle is NULL");
-    unsigned long long bad = 0;
+    unsigned long long bad = 0, late = 0;
     COLOR_CK(cudaMemcpyAsync(&bad, c->nonfinite, sizeof bad, cudaMemcpyDeviceToHost, c->st));
+    COLOR_CK(cudaMemcpyAsync(&late, c->timeouts, sizeof late, cudaMemcpyDeviceToHost, c->st));
     COLOR_CK(cudaStreamSynchronize(c->st));
+    if (late) return cfail(QQA_ETIMEOUT, "%llu bounded waits of the tensor-core neighbour sums ran out", late);
     if (bad) return cfail(QQA_ENONFINITE, "%llu non-finite second moments in the colouring state", bad);
     return QQA_OK;
 }

@@ -73,7 +73,8 @@ def test_color_init_is_the_oracle_draw(K, S):
 @pytest.mark.parametrize("S", [8, 37, 300])
 def test_color_single_step_matches_oracle(gen, K, S):
     """Cold moments at t = 0, warm moments at t = 60, with the communication term on.
-    Graphs of up to 1600 nodes take the shared-memory neighbour sums, the
+    The dense graph of 112 nodes or more (queen13-13) takes the tensor-core
+    neighbour sums, the other small graphs the shared-memory ones, the sparse
     2000-node graph the direct gather."""
     if gen == "er_large":
         g = G.erdos_renyi(2000, 0.005, 9)
@@ -89,9 +90,9 @@ def test_color_single_step_matches_oracle(gen, K, S):
 def test_color_graph_replay_equals_single_launches():
     """Chunks of steps replayed from a captured CUDA graph (the step index read
     from the device counter) give the same state, bit for bit, as the same
-    steps launched one at a time, for both the shared-memory and the direct
-    neighbour sums."""
-    for g, K in ((G.queens(6, 6), 7), (G.erdos_renyi(1700, 0.004, 2), 5)):
+    steps launched one at a time, for the shared-memory, tensor-core and
+    direct neighbour sums."""
+    for g, K in ((G.queens(6, 6), 7), (G.queens(11, 11), 11), (G.erdos_renyi(1700, 0.004, 2), 5)):
         p = Params(S=96, steps=200, lr=0.1, alpha_comm=0.2, seed=4, precision=FP32)
         a = qqa.Coloring(g, K, qqa.make_params(p))
         b = qqa.Coloring(g, K, qqa.make_params(p))

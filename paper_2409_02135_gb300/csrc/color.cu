@@ -7,22 +7,28 @@
 // [0,1]). Rows of one (i, k) are S_pad = S rounded up to 32 floats long, so a
 // warp reads 128 contiguous bytes of one colour plane.
 //
-// One step is two launches (one for graphs above 1600 nodes):
-//   color_gather_kernel  Y = A sigma, the neighbour sums of the relaxed
-//                        conflicts, as a sparse-times-dense product over the
-//                        columns (k, s) of sigma staged in shared memory
-//                        (graphs of up to 1600 nodes; larger graphs gather
-//                        from global memory inside the update kernel)
-//   color_update_kernel  one block per node, four replicas per thread:
+// One step is the neighbour sums and the update:
+//   neighbour sums  Y = A sigma, the relaxed-conflict sums, one of
+//                   - color_planes_kernel + color_gather_tc_kernel: dense
+//                     graphs (>= 5% of node pairs are edges) of 112 to 4096
+//                     nodes, on the tensor cores (tcgen05);
+//                   - color_gather_kernel: graphs of up to 1600 nodes, a
+//                     sparse product over the columns (k, s) of sigma staged
+//                     in shared memory;
+//                   - larger graphs: gathered from global memory inside the
+//                     update kernel;
+//   color_update_kernel  one block per (node, 128 replicas), warp k = colour k,
+//                        four replicas per lane:
+//     statistics  mean and STD_eps of sigma_ik over the replicas, from the
+//                 partial sums the previous step left
 //     gradient    g_ik = Y_ik                                           relaxed conflicts
 //                      + gamma_t (-c_K a K) (K sigma_ik - 1)^(a-1)      entropy s_K (App. B)
 //                      - alpha (sigma_ik - mean_ik) / STD_ik            communication (Eq. 10)
 //                 dR/dW_ik = (g_ik - sum_k' sigma_ik' g_ik') / sum_k W_ik   (Clamp-normalise chain rule)
 //     update      AdamW with decoupled decay, + sqrt(2 lr T) xi, projection to [0,1]
 //     relaxation  sigma' = W' / sum_k W' (a zero row: 1/K), into the other buffer,
-//                 with the row sums sum_k W' for the next chain rule
-//     statistics  mean and STD_eps of sigma' over the replicas of each (i, k)
-//                 for the next step's communication term (two block reductions)
+//                 with the row sums sum_k W' for the next chain rule and the
+//                 partial replica sums of sigma' for the next statistics
 // sigma is double-buffered: a step reads sigma^t of the neighbours and writes
 // sigma^{t+1} of its own node, so every block sees one consistent state.
 //

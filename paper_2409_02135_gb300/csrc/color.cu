@@ -201,6 +201,16 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
     }
 
     float g[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sg[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // this lane's own state and noise, requested before the first barrier so
+    // their latency overlaps the gradient and the exchange of the products
+    float4 w4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), m4 = w4, v4 = w4, rs = w4;
+    float xi[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) {
+        w4 = ld4(W + idx);
+        m4 = ld4(M + idx);
+        v4 = ld4(V + idx);
+        rs = ld4(rsum + (size_t)i * plane + s0);
+    }
     if (live) {
         // relaxed conflicts Y_ik
         if (Ygat) {
@@ -224,6 +234,7 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
             for (int h = 0; h < a.half_pow; ++h) upow *= u2;
             g[e] = fmaf(coef, sg[e] - mean, fmaf(sc.x, upow, g[e]));
         }
+        if (a.noise_scale != 0.0f) gauss4(a.seed_lo, a.seed_hi, (uint32_t)(i * K + k), (uint32_t)q, (uint32_t)t, xi);
     }
     xk[k][lane] = make_float4(sg[0] * g[0], sg[1] * g[1], sg[2] * g[2], sg[3] * g[3]);
     __syncthreads();
@@ -235,12 +246,7 @@ color_update_kernel(ColorStepArgs a, int32_t chunks, const int32_t *__restrict__
     float wn[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (live) {
         // chain rule through W / sum W, AdamW, noise, projection
-        const float4 rs = ld4(rsum + (size_t)i * plane + s0);
         const float rsv[4] = {rs.x, rs.y, rs.z, rs.w};
-        float xi[4];
-        if (a.noise_scale != 0.0f) gauss4(a.seed_lo, a.seed_hi, (uint32_t)(i * K + k), (uint32_t)q, (uint32_t)t, xi);
-        else xi[0] = xi[1] = xi[2] = xi[3] = 0.0f;
-        const float4 w4 = ld4(W + idx), m4 = ld4(M + idx), v4 = ld4(V + idx);
         const float w0[4] = {w4.x, w4.y, w4.z, w4.w}, m0[4] = {m4.x, m4.y, m4.z, m4.w},
                     v0[4] = {v4.x, v4.y, v4.z, v4.w};
         float gw[4], mn[4], vn[4];

@@ -385,7 +385,12 @@ const char *qqa_noalloc_last_error(void);
  * i*K + k. Rounding: x_is = argmax_k sigma_iks (ties to the lowest colour);
  * the cost of a replica is its number of edges {i, j} with x_is = x_js.
  * The state lives in device memory owned by the handle: W, m, v and two
- * buffers of sigma, each n * K * ceil(S/32)*32 floats. FP32 only.
+ * buffers of sigma, each n * K * ceil(S/32)*32 floats, the neighbour sums in
+ * the same size (graphs of up to 1600 nodes, and dense graphs), and for dense
+ * graphs of 112 to 4096 nodes (at least 5% of node pairs are edges) an fp16
+ * adjacency of n_pad^2 and two fp16 planes of sigma of n_pad * K * S_pad
+ * (n_pad = n rounded up to 128), which the tensor cores use for the
+ * neighbour sums. FP32 only.
  */
 #define QQA_COLOR_MAX_K 32
 typedef struct qqa_color qqa_color;
@@ -408,7 +413,8 @@ void qqa_color_destroy(qqa_color *c);
 /* Enqueue up to nsteps steps (fewer when the schedule ends); *done (optional)
  * receives the count. Asynchronous. */
 int qqa_color_steps(qqa_color *c, int32_t nsteps, int32_t *done);
-/* Wait for the stream; QQA_ENONFINITE if a step produced a non-finite moment. */
+/* Wait for the stream; QQA_ENONFINITE if a step produced a non-finite moment,
+ * QQA_ETIMEOUT if a bounded device wait of the tensor-core path ran out. */
 int qqa_color_sync(qqa_color *c);
 /* One step that also writes dR/dW of that step to the HOST array grad[n][K][S]. */
 int qqa_color_step_debug(qqa_color *c, float *grad);

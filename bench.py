@@ -83,7 +83,8 @@ def read_peak():
 
 # device symbol of each step kernel variant (as ncu lists it)
 KERNEL_SYMBOL = {"direct": "qqa_step_kernel", "staged": "qqa_step_tiled_kernel", "stream": "qqa_step_stream_kernel",
-                 "dense": "qqa_step_dense_kernel", "pipe": "qqa_step_pipe_kernel"}
+                 "dense": "qqa_step_dense_kernel", "pipe": "qqa_step_pipe_kernel", "scalar": "qqa_step_scalar_kernel"}
+KERNEL_NAMES = ["auto", "direct", "staged", "stream", "dense", "pipe", "scalar"]
 
 
 def read_tensor_peak():
@@ -359,7 +360,7 @@ def run_ours(args):
     kinds = [inst.kind for inst in wl.instances]
     probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
     params = [qqa.make_params(inst.params) for inst in wl.instances]
-    cfg = qqa.LaunchConfig(use_graphs=1, kernel={"auto": 0, "direct": 1, "staged": 2, "stream": 3, "dense": 4, "pipe": 5}[args.kernel],
+    cfg = qqa.LaunchConfig(use_graphs=1, kernel=KERNEL_NAMES.index(args.kernel),
                            kernel_param=args.kernel_param, group_lanes=args.group_lanes,
                            vec_per_lane=args.vec_per_lane, block_threads=args.block_threads)
     tuned_us = None
@@ -418,7 +419,7 @@ def run_ours(args):
     alg_bytes = algorithmic_bytes_per_launch(wl)
     peak, peak_kind = read_peak()
     achieved = alg_bytes / avg_launch_s / 1e9
-    variant = ["auto", "direct", "staged", "stream", "dense", "pipe"][run.config().kernel]
+    variant = KERNEL_NAMES[run.config().kernel]
     tensor = None
     if variant == "dense":
         # the tensor-core step's contraction: A (n_pad^2, fp16) times two fp16 planes of width N
@@ -542,7 +543,7 @@ def run_ours(args):
         bf16 = {"value": value_b, "unit": METRIC, "ms_per_step": statistics.mean(msb),
                 "over_plain_fp32": value_b / plain["value"],
                 "time_to_oracle_quality": time_to_quality(args.workload, run_b, len(probs), start_b, ev_b, R),
-                "launch": ["auto", "direct", "staged", "stream", "dense", "pipe"][run_b.config().kernel]}
+                "launch": KERNEL_NAMES[run_b.config().kernel]}
         run_b.close()
 
     prec = wl.instances[0].params.precision
@@ -554,7 +555,7 @@ def run_ours(args):
                    "anneal_steps": K, "round_every": R, "precision": "fp32" if prec == W.FP32 else "bf16",
                    "l2": "flushed between timed anneals (512 MB write)",
                    "parallelism": f"instances x{world} ranks" if world > 1 else "single GPU",
-                   "launch": {"kernel": ["auto", "direct", "staged", "stream", "dense", "pipe"][run.config().kernel],
+                   "launch": {"kernel": KERNEL_NAMES[run.config().kernel],
                               "group_lanes": run.config().group_lanes, "vec_per_lane": run.config().vec_per_lane,
                               "kernel_param": run.config().kernel_param,
                               "block_threads": run.config().block_threads, "grid_blocks": run.config().grid_blocks,
@@ -780,7 +781,7 @@ def main():
                     help="mis_er700_800 (default), mis_er100, maxcut_regular3, maxcut_ba4, mis_cliqueblocks512, "
                          "serving, coloring (Table 9 graphs), or mis_rrg_d<d>_n<n>[_x<graphs>][_K<steps>] "
                          "(S = 1 random regular graphs)")
-    ap.add_argument("--kernel", choices=["auto", "direct", "staged", "stream", "dense", "pipe"], default="auto")
+    ap.add_argument("--kernel", choices=KERNEL_NAMES, default="auto")
     ap.add_argument("--kernel-param", type=int, default=0)
     ap.add_argument("--group-lanes", type=int, default=0)
     ap.add_argument("--vec-per-lane", type=int, default=0)

@@ -107,9 +107,20 @@ typedef struct qqa_params {
  *                 or QQA_KERNEL_PIPE (sparse graphs: every warp bulk-copies
  *                 the next rows it owns of p, m and v into its own shared-
  *                 memory double buffer while it updates the current ones)
+ *                 QQA_KERNEL_SCALAR: runs whose instances all have S = 1 (the
+ *                 paper's setting for random regular graphs, Sec. 5.1) always
+ *                 use it, and no other kernel: the state is one value per node,
+ *                 without padding, and kernel_param lanes (4, 8, 16, 32) share
+ *                 one node's neighbour list in the sparse product
+ *   Rows whose degree exceeds max(64, 8 x the graph's mean degree) are updated
+ *   by a separate long-row kernel launched with the gather kernels: their
+ *   neighbour lists are summed in segments of 32 CSR entries by separate lane
+ *   groups, then combined in segment order (FP32), so a hub of a scale-free
+ *   graph does not hold up the step.
  *   kernel_param: staged: row groups per warp (2, 4, 8);
  *                 stream: neighbour rows prefetched per row (4, 8);
- *                 dense: reported MMA width (64, 128, 256)
+ *                 dense: reported MMA width (64, 128, 256);
+ *                 scalar: lanes per node row in the sparse product
  */
 #define QQA_KERNEL_AUTO 0
 #define QQA_KERNEL_DIRECT 1
@@ -117,6 +128,7 @@ typedef struct qqa_params {
 #define QQA_KERNEL_STREAM 3
 #define QQA_KERNEL_DENSE 4
 #define QQA_KERNEL_PIPE 5
+#define QQA_KERNEL_SCALAR 6
 typedef struct qqa_launch_config {
     int32_t group_lanes;
     int32_t vec_per_lane;
@@ -172,13 +184,16 @@ int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, con
  * Add one instance: allocate X (two buffers), the FP32 master (BF16 runs),
  * AdamW moments m, v, and evaluation buffers; then draw the initial state
  * p ~ U(0,1] from Philox (seed, node, replica) and zero m, v (step t = 0).
+ * The paper does not state the initial state (Sec. 3.2 starts the relaxed
+ * variables in [0,1]^N); the uniform draw is this library's reading, and the
+ * moments start at zero as AdamW defines them (Sec. 3.4, App. C.3).
  * The problem must outlive the run. Returns the slot index.
  * Errors: QQA_EINVAL (S > S_max, bad params), QQA_EBUSY (no free slot), QQA_ENOMEM.
  */
 int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void *stream, int32_t *slot);
 /*
  * Restart one slot (slot >= 0) or every active slot (slot = -1) from a fresh
- * initial state drawn with `seed` (step t = 0, m = v = 0, history cleared),
+ * initial state drawn with `seed` (the same draw as qqa_run_add) (step t = 0, m = v = 0, history cleared),
  * keeping its allocations. Asynchronous except for a small descriptor upload.
  */
 int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stream);
@@ -209,16 +224,31 @@ int qqa_autotune(qqa_problem *const *problems, const qqa_params *params, int32_t
  * Advance every active, unfinished instance by up to `nsteps` annealing steps
  * (one fused kernel launch per step; replayed from a CUDA graph when
  * use_graphs is set). An instance stops at its own `steps`. Asynchronous.
+ * One step is the update of Sec. 3.2-3.4: the gradient of the relaxed energy
+ * (MIS Eq. 22, max-clique Eq. 24, max-cut Eq. 26 of App. D.1) plus gamma_t
+ * times the gradient of the alpha-entropy (Eq. 7, gamma_t linear over the
+ * instance's steps, App. C.2) and the communication term (Eq. 10); the AdamW
+ * update that replaces the gradient step of Eq. 11 (Sec. 3.4, App. C.3) with
+ * the Langevin noise sqrt(2 lr T) xi; and the projection to [0, 1] (Sec. 5
+ * "Implementation").
+ * Errors: QQA_EINVAL (NULL run, nsteps < 0), QQA_ECUDA.
  */
 int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream);
 /*
  * Projection rounding and exact costs of every replica of every active
  * instance (asynchronous); appends each instance's best feasible objective to
  * its history. Results are read with qqa_run_result after qqa_run_sync.
+ * The rounding x = [p > 1/2] is the step function the paper applies after
+ * annealing (Sec. 5 "Implementation"); the costs are the discrete energies of
+ * App. D.1 in integers (independent-set size and edges inside x, cut weight,
+ * clique size and missing edges).
  */
 int qqa_run_eval(qqa_run *r, void *stream);
 /* Wait for the stream, copy the latest evaluation to host mirrors, and check
- * the device status word (QQA_ENONFINITE if a non-finite value was seen). */
+ * the device status word: QQA_ETIMEOUT if a bounded device wait of the staged,
+ * pipelined or tensor-core step ran out (that step left its rows unchanged),
+ * else QQA_ENONFINITE if a non-finite value was seen. The status word is not
+ * cleared: a run that reported an error keeps reporting it. */
 int qqa_run_sync(qqa_run *r, void *stream);
 /*
  * Latest evaluation of one slot (after qqa_run_sync). Any pointer may be NULL.
@@ -234,7 +264,8 @@ int qqa_run_result(const qqa_run *r, int32_t slot, int64_t *obj, int64_t *viol, 
                    double *energy, int32_t *best_s, uint32_t *best_x, int32_t *step);
 /*
  * Best feasible objective after each evaluation of a slot (INT64_MIN when no
- * replica was feasible) and the step count it was taken at. `cap` entries at
+ * replica was feasible) and the step count it was taken at (the periodic
+ * rounding during the anneal, Sec. 5 "Implementation"). `cap` entries at
  * most; *count receives the number available. Reads host mirrors (after sync).
  */
 int qqa_run_history(const qqa_run *r, int32_t slot, int32_t cap, int64_t *best_obj, int32_t *at_step,
@@ -243,16 +274,29 @@ int qqa_run_history(const qqa_run *r, int32_t slot, int32_t cap, int64_t *best_o
 int qqa_run_slot_step(const qqa_run *r, int32_t slot, int32_t *t);
 
 /*
- * Whole anneal of a batch, as the paper runs it: create the run, init, K
- * steps with a periodic evaluation every round_every steps, and a final
- * evaluation; then synchronise. The run stays alive for reading results.
+ * Whole anneal of a batch, as the paper runs it (Sec. 3.2-3.4 for the step,
+ * Sec. 5 "Implementation" and App. C.2-C.3 for the schedule, the optimizer and
+ * the final rounding): create the run, init, K steps with a periodic
+ * evaluation every round_every steps, and a final evaluation; then
+ * synchronise. The run stays alive for reading results (*out, to be released
+ * with qqa_run_destroy; the problems must outlive it).
+ * Errors: as qqa_run_create and qqa_run_steps; QQA_ETIMEOUT from the final
+ * synchronisation destroys the run. QQA_ENONFINITE still returns the run in
+ * *out, so its (clamped) results can be read.
  */
 int qqa_anneal(qqa_problem *const *problems, const qqa_params *params, int32_t count,
                const qqa_launch_config *cfg, const qqa_allocator *alloc, void *stream, qqa_run **out);
 /*
  * Evaluate (qqa_run_eval + qqa_run_sync) and copy the results of every active
  * slot, concatenated in slot order: obj/viol/feasible/energy have sum(S_k)
- * entries, best_s has one per slot, best_x sum(ceil(n_k/32)) words.
+ * entries, best_s has one per slot, best_x sum(ceil(n_k/32)) words. All are
+ * HOST arrays allocated by the caller; any may be NULL.
+ * This is the rounding of Sec. 5 "Implementation" (x = [p > 1/2], taken from
+ * the FP32 state or master) with the exact discrete costs of App. D.1; the
+ * best replica is the feasible one with the largest objective, ties to the
+ * lowest index. Synchronises `stream`.
+ * Errors: QQA_EINVAL, QQA_ECUDA, QQA_ETIMEOUT; QQA_ENONFINITE after copying the
+ * results.
  */
 int qqa_round_eval(qqa_run *r, void *stream, int64_t *obj, int64_t *viol, uint8_t *feasible, double *energy,
                    int32_t *best_s, uint32_t *best_x);
@@ -275,8 +319,16 @@ int qqa_run_set_state(qqa_run *r, int32_t slot, void *stream, const float *X, co
                       int32_t t);
 /*
  * One step of every active instance that also writes the gradient g of slot
- * `slot` (all terms, before AdamW) to host grad[n][S]. Synchronises.
+ * `slot` (all terms, before AdamW: Eq. 22/24/26 + gamma_t Eq. 7 + Eq. 10) to
+ * host grad[n][S]. Synchronises.
  */
+/*
+ * Test hook (the paper has no counterpart): overwrite the run's device status
+ * word with the given counts of non-finite values and of bounded waits that
+ * ran out, so that the reporting of qqa_run_sync can be checked without
+ * making a kernel fail. Synchronises.
+ */
+int qqa_run_debug_set_status(qqa_run *r, uint64_t nonfinite, uint64_t timeouts, void *stream);
 int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
 
 /* ---------------------------------------------------------- serving */
@@ -418,6 +470,10 @@ int qqa_color_steps(qqa_color *c, int32_t nsteps, int32_t *done);
 int qqa_color_sync(qqa_color *c);
 /* One step that also writes dR/dW of that step to the HOST array grad[n][K][S]. */
 int qqa_color_step_debug(qqa_color *c, float *grad);
+/* Test hook (the paper has no counterpart): overwrite the handle's device
+ * counters of non-finite moments and of bounded waits that ran out, so that
+ * the reporting of qqa_color_sync can be checked. Synchronises. */
+int qqa_color_debug_set_status(qqa_color *c, uint64_t nonfinite, uint64_t timeouts);
 /* HOST copies [n][K][S] (element ((i*K + k)*S + s)) of W, m, v (any may be
  * NULL) and the step counter. Synchronous. */
 int qqa_color_get_state(qqa_color *c, float *W, float *m, float *v, int32_t *t);

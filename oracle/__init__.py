@@ -7,8 +7,8 @@ library (paper_2409_02135_gb300), and that library never imports it.
 
 The arithmetic lives in qqa_oracle.c (plain loops in double precision, one
 element at a time, in the order the paper states the method); this module
-only marshals numpy arrays to it. Parity status of each function is recorded
-in the design doc; every function here is pinned by tests/test_oracle_pins.py.
+only marshals numpy arrays to it. Every function here is pinned by
+tests/test_oracle_pins.py against what the paper and the mathematics fix.
 """
 from __future__ import annotations
 

@@ -19,7 +19,7 @@
  * Layout: X[i*S + s] = p_i^{(s)} (node-major, S contiguous), CSR adjacency
  * (row_ptr[n+1], col[nnz], optional integer weights w[nnz]; NULL = unit).
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - STD uses the population normalisation of Eq. 10 and sqrt(var + comm_eps)
  *     so the derivative exists when all S values coincide.
  *   - AdamW: decoupled weight decay p *= 1 - lr*wd, then the bias-corrected
@@ -455,7 +455,7 @@ int32_t oracle_anneal(const oracle_params *P, int32_t n, const int32_t *rp, cons
 /* State W[i][k][s] in [0,1] (node i, colour k, replica s), flattened   */
 /* as ((i * K + k) * S + s). sigma_ik = W_ik / sum_k' W_ik' (the clamp  */
 /* is the identity on [0,1]; a row of zeros maps to 1/K).               */
-/* Readings where the paper is silent (also listed in the design doc):       */
+/* Readings where the paper is silent:                                   */
 /*   - after each update W is projected to [0,1], as p is in the binary */
 /*     method; sigma is re-formed from the projected W;                 */
 /*   - the communication term acts on sigma, per (node, colour), over   */

@@ -18,7 +18,7 @@ import ctypes
 import numpy as np
 
 from ._lib import (  # noqa: F401
-    BF16, FP32, KERNEL_AUTO, KERNEL_DENSE, KERNEL_DIRECT, KERNEL_PIPE, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_OK,
+    BF16, FP32, KERNEL_AUTO, KERNEL_DENSE, KERNEL_DIRECT, KERNEL_PIPE, KERNEL_SCALAR, KERNEL_STAGED, KERNEL_STREAM, MAXCLIQUE, MAXCUT, MIS, QQA_EBUSY, QQA_ECUDA, QQA_EINVAL, QQA_ENOMEM, QQA_ENONFINITE, QQA_ETIMEOUT, QQA_OK,
     QQAError, check, load, qqa_allocator, qqa_launch_config, qqa_params, qqa_request_info, ALLOC_FN, FREE_FN,
     SIGNATURES, REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED,
 )
@@ -271,6 +271,10 @@ class Run:
         check(load().qqa_run_step_debug(self.handle, slot, stream_handle(self.stream), _ptr(g, ctypes.c_float)))
         return g
 
+    def debug_set_status(self, nonfinite: int = 0, timeouts: int = 0):
+        """Test hook: overwrite the device status word that sync() reports."""
+        check(load().qqa_run_debug_set_status(self.handle, int(nonfinite), int(timeouts), stream_handle(self.stream)))
+
 
 def autotune(problems, params, trial_steps: int = 100, stream=None, allocator=None):
     """qqa_autotune: the fastest launch shape for these instances (cached per
@@ -417,6 +421,10 @@ class Coloring:
         g = np.empty((self.n, self.K, self.S), np.float32)
         check(load().qqa_color_step_debug(self.handle, _ptr(g, ctypes.c_float)))
         return g
+
+    def debug_set_status(self, nonfinite: int = 0, timeouts: int = 0):
+        """Test hook: overwrite the device counters that sync() reports."""
+        check(load().qqa_color_debug_set_status(self.handle, int(nonfinite), int(timeouts)))
 
     def get_state(self):
         W, m, v = (np.empty((self.n, self.K, self.S), np.float32) for _ in range(3))

@@ -23,7 +23,7 @@ ERROR_NAMES = {QQA_EINVAL: "EINVAL", QQA_ENOMEM: "ENOMEM", QQA_ECUDA: "ECUDA", Q
 
 MIS, MAXCUT, MAXCLIQUE = 0, 1, 2
 FP32, BF16 = 0, 1
-KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, KERNEL_DENSE, KERNEL_PIPE = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_STAGED, KERNEL_STREAM, KERNEL_DENSE, KERNEL_PIPE, KERNEL_SCALAR = 0, 1, 2, 3, 4, 5, 6
 
 
 class qqa_params(ctypes.Structure):
@@ -104,6 +104,7 @@ SIGNATURES = {
     "qqa_run_get_state": (ctypes.c_int, [_P, _I32, _P, _PF, _PF, _PF, _PI32]),
     "qqa_run_set_state": (ctypes.c_int, [_P, _I32, _P, _PF, _PF, _PF, _I32]),
     "qqa_run_step_debug": (ctypes.c_int, [_P, _I32, _P, _PF]),
+    "qqa_run_debug_set_status": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64, _P]),
     "qqa_round_eval_noalloc": (ctypes.c_int, [_I32, _I32, ctypes.c_int64, _P, _P, _P, _I32, ctypes.c_int64, _P,
                                               ctypes.c_float, _P, _P, _P, _P, _P, _P]),
     "qqa_noalloc_last_error": (ctypes.c_char_p, []),
@@ -112,6 +113,7 @@ SIGNATURES = {
     "qqa_color_steps": (ctypes.c_int, [_P, _I32, _PI32]),
     "qqa_color_sync": (ctypes.c_int, [_P]),
     "qqa_color_step_debug": (ctypes.c_int, [_P, _PF]),
+    "qqa_color_debug_set_status": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64]),
     "qqa_color_get_state": (ctypes.c_int, [_P, _PF, _PF, _PF, _PI32]),
     "qqa_color_set_state": (ctypes.c_int, [_P, _PF, _PF, _PF, _I32]),
     "qqa_color_round": (ctypes.c_int, [_P, _PI64, _PI32, _PU8]),

@@ -37,6 +37,9 @@ StepFn step_dense_kernel_fp32(int N);
 using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
 PipeFn step_pipe_kernel_fp32(int G, int VPL);
 PipeFn step_pipe_kernel_bf16(int G, int VPL);
+StepFn step_hub_kernel_fp32(int G, int VPL);
+StepFn step_hub_kernel_bf16(int G, int VPL);
+StepFn step_scalar_kernel(int prec, int L);
 int dense_threads();
 int dense_smem_bytes(int N);
 }  // namespace qqa
@@ -107,8 +110,21 @@ struct qqa_problem {
     int64_t nnz = 0;
     int32_t max_abs_w = 1;   // largest |edge weight| (1 when unweighted)
     int32_t *row_ptr = nullptr, *col = nullptr, *w = nullptr;
+    // long rows: degree above long_thresh, summed in segments of kSegLen
+    // neighbours by the long-row kernel (device tables; none when nlong = 0)
+    int32_t long_thresh = 0x7fffffff, nlong = 0, nseg = 0;
+    int32_t *long_rows = nullptr, *seg_ptr = nullptr, *seg_row = nullptr;
     Alloc alloc;
 };
+
+// A row is long when its degree exceeds max(64, 8 x the mean degree rounded
+// up): on graphs with hubs (scale-free degree distributions) such a row would
+// take a lane group many times longer than a typical row.
+static int32_t long_row_threshold(int32_t n, int64_t nnz)
+{
+    const int64_t mean_up = (nnz + n - 1) / std::max<int32_t>(n, 1);
+    return (int32_t)std::min<int64_t>(0x7fffffff, std::max<int64_t>(64, 8 * mean_up));
+}
 
 // ------------------------------------------------------------------- misc
 extern "C" const char *qqa_last_error(void) { return g_last_error.c_str(); }
@@ -198,10 +214,28 @@ extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_pt
     if (w)
         for (int64_t k = 0; k < p->nnz; ++k) p->max_abs_w = std::max(p->max_abs_w, w[k] < 0 ? -w[k] : w[k]);
     p->alloc = Alloc::from(alloc);
+    // long rows and their segments
+    std::vector<int32_t> lrows, lseg_ptr{0}, lseg_row;
+    p->long_thresh = long_row_threshold(n, p->nnz);
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t deg = row_ptr[i + 1] - row_ptr[i];
+        if (deg <= p->long_thresh) continue;
+        const int32_t nsegs = (deg + kSegLen - 1) / kSegLen;
+        for (int32_t q = 0; q < nsegs; ++q) lseg_row.push_back((int32_t)lrows.size());
+        lrows.push_back(i);
+        lseg_ptr.push_back(lseg_ptr.back() + nsegs);
+    }
+    p->nlong = (int32_t)lrows.size();
+    p->nseg = (int32_t)lseg_row.size();
     p->row_ptr = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)(n + 1), st);
     p->col = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
     if (w) p->w = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
-    if (!p->row_ptr || !p->col || (w && !p->w)) {
+    if (p->nlong) {
+        p->long_rows = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)p->nlong, st);
+        p->seg_ptr = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)(p->nlong + 1), st);
+        p->seg_row = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)p->nseg, st);
+    }
+    if (!p->row_ptr || !p->col || (w && !p->w) || (p->nlong && (!p->long_rows || !p->seg_ptr || !p->seg_row))) {
         qqa_destroy_problem(p);
         return fail(QQA_ENOMEM, "device allocation for the graph failed");
     }
@@ -210,6 +244,12 @@ extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_pt
         e = cudaMemcpyAsync(p->col, col, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && w && p->nnz)
         e = cudaMemcpyAsync(p->w, w, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && p->nlong)
+        e = cudaMemcpyAsync(p->long_rows, lrows.data(), sizeof(int32_t) * lrows.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && p->nlong)
+        e = cudaMemcpyAsync(p->seg_ptr, lseg_ptr.data(), sizeof(int32_t) * lseg_ptr.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && p->nlong)
+        e = cudaMemcpyAsync(p->seg_row, lseg_row.data(), sizeof(int32_t) * lseg_row.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host arrays may be freed after return
     if (e != cudaSuccess) {
         qqa_destroy_problem(p);
@@ -234,6 +274,9 @@ extern "C" void qqa_destroy_problem(qqa_problem *p)
     p->alloc.put(p->row_ptr, 0);
     p->alloc.put(p->col, 0);
     p->alloc.put(p->w, 0);
+    p->alloc.put(p->long_rows, 0);
+    p->alloc.put(p->seg_ptr, 0);
+    p->alloc.put(p->seg_row, 0);
     delete p;
 }
 
@@ -259,6 +302,15 @@ struct qqa_run {
     qqa_launch_config cfg{};
     int32_t rows_per_tile = 0, max_grid = 0, smem = 0;
     StepFn step_fn = nullptr;
+    bool scalar = false;              // one replica per instance: state p[n], scalar kernel
+    int32_t mean_deg_hint = 0;        // mean degree of the instances (scalar kernel's lanes per row)
+    StepFn hub_fn = nullptr;          // long-row kernel for the (G, VPL) of the step kernel
+    int32_t hub_max_grid = 0;
+    Tile *d_hub_items = nullptr;      // (slot, segment) work items of the long-row kernel
+    int32_t hub_cap = 0, num_hub_items = 0, hub_grid = 0;
+    int32_t *d_clique_slots = nullptr;   // active max-clique slots (column sums after every step)
+    int32_t clique_cap = 0, num_clique = 0;
+    int32_t kernels_per_step = 1;
     bool dynamic = false;             // slots come and go: always launch the full persistent grid
     int32_t dense_N = 0;              // > 0: tensor-core step (MMA width = replicas covered)
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
@@ -270,8 +322,8 @@ struct qqa_run {
     std::vector<InstDesc> h_descs;
     Tile *d_tiles = nullptr;
     int32_t tile_cap = 0;
-    int32_t *d_num_tiles = nullptr;  // [0] tiles, [1] streaming cache hints on (state larger than L2)
-    int32_t tile_words[2] = {0, 0};
+    int32_t *d_num_tiles = nullptr;  // [0] tiles, [1] streaming cache hints on (state larger than L2), [2] long-row items
+    int32_t tile_words[4] = {0, 0, 0, 0};
     int32_t num_tiles = 0;
     RunStatus *d_status = nullptr;
     float *d_scratch = nullptr;   // state import/export staging
@@ -300,10 +352,63 @@ static int pick_layout(int32_t S_pad, int32_t vec, int32_t &G, int32_t &VPL)
 }
 
 // staged_hint: 1 if the graphs favour the staged kernel (auto mode), else 0.
+static int resolve_scalar(qqa_run *r, qqa_launch_config c)
+{
+    if (c.kernel != QQA_KERNEL_AUTO && c.kernel != QQA_KERNEL_SCALAR)
+        return fail(QQA_EINVAL, "runs of one replica per instance use the scalar kernel (QQA_KERNEL_SCALAR)");
+    int L = c.kernel_param;
+    if (L == 0) {
+        const int md = r->mean_deg_hint;
+        L = md <= 6 ? 4 : (md <= 24 ? 8 : (md <= 64 ? 16 : 32));
+    }
+    r->step_fn = step_scalar_kernel(r->prec, L);
+    if (!r->step_fn) return fail(QQA_EINVAL, "no scalar kernel with %d lanes per row (4, 8, 16, 32)", L);
+    const int block = c.block_threads ? c.block_threads : 256;
+    if (block < 32 || block > 256 || block % 32)
+        return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
+    int dev = 0, sms = 0, occ = 0;
+    QQA_CK(cudaGetDevice(&dev));
+    QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block, 0));
+    if (occ < 1) return fail(QQA_EINVAL, "scalar kernel cannot run %d threads per block", block);
+    r->scalar = true;
+    r->tiled_fn = nullptr;
+    r->pipe_fn = nullptr;
+    r->hub_fn = nullptr;
+    r->dense_N = 0;
+    r->smem = 0;
+    r->rows_per_tile = block;   // 32 rows per warp
+    c.group_lanes = L;
+    c.vec_per_lane = 1;
+    c.block_threads = block;
+    c.kernel = QQA_KERNEL_SCALAR;
+    c.kernel_param = L;
+    r->max_grid = c.grid_blocks ? c.grid_blocks : sms * occ;
+    c.grid_blocks = r->max_grid;
+    r->cfg = c;
+    return QQA_OK;
+}
+
+// The long-row kernel of the step kernel's (G, VPL), for runs that gather
+// neighbour rows (not the tensor-core or scalar steps).
+static int resolve_hub(qqa_run *r, int32_t G, int32_t VPL)
+{
+    r->hub_fn = r->prec == kFP32 ? step_hub_kernel_fp32(G, VPL) : step_hub_kernel_bf16(G, VPL);
+    if (!r->hub_fn) return fail(QQA_EINVAL, "no long-row kernel for G=%d VPL=%d", G, VPL);
+    int dev = 0, sms = 0, occ = 0;
+    QQA_CK(cudaGetDevice(&dev));
+    QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->hub_fn, 256, 0));
+    if (occ < 1) return fail(QQA_EINVAL, "long-row kernel G=%d VPL=%d does not fit on an SM", G, VPL);
+    r->hub_max_grid = sms * occ;
+    return QQA_OK;
+}
+
 static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_hint)
 {
     qqa_launch_config c{};
     if (cfg) c = *cfg;
+    if (r->S_max == 1) return resolve_scalar(r, c);
     int32_t G = c.group_lanes, VPL = c.vec_per_lane;
     if (G == 0 || VPL == 0) {
         int32_t g2, v2;
@@ -320,6 +425,7 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     if (mode == QQA_KERNEL_AUTO) mode = QQA_KERNEL_DIRECT;
     if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_PIPE) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
     r->pipe_fn = nullptr;
+    r->hub_fn = nullptr;
     if (mode == QQA_KERNEL_DENSE) {
         if (r->prec != kFP32) return fail(QQA_EINVAL, "the dense tensor-core step needs an FP32 run");
         const int N = r->S_max_pad <= 64 ? 64 : (r->S_max_pad <= 128 ? 128 : (r->S_max_pad <= 256 ? 256 : 0));
@@ -366,8 +472,8 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         const int row_bytes = r->S_max_pad * tb;
         r->chunk_rows = std::max(8, 32768 / row_bytes);
         r->buf_elems = r->chunk_rows * r->S_max_pad;
-        // header, two chunk buffers, clique partial sums (1024 floats), CSR index segment
-        r->smem = 128 + 2 * r->buf_elems * tb + 1024 * (int)sizeof(float) + kTiledIdxCapHost * (int)sizeof(int32_t);
+        // header, two chunk buffers, CSR index segment
+        r->smem = 128 + 2 * r->buf_elems * tb + kTiledIdxCapHost * (int)sizeof(int32_t);
         QQA_CK(cudaFuncSetAttribute(r->tiled_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
         QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->tiled_fn, block, r->smem));
         r->rows_per_tile = (block / 32) * rpw * (32 / G);
@@ -423,7 +529,7 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         rpw = 0;
         r->step_fn = r->prec == kFP32 ? step_kernel_fp32(G, VPL) : step_kernel_bf16(G, VPL);
         if (!r->step_fn) return fail(QQA_EINVAL, "no step kernel for G=%d VPL=%d precision %d", G, VPL, r->prec);
-        r->smem = r->S_max_pad * (int)sizeof(float);
+        r->smem = 0;
         if (c.block_threads == 0) {
             // registers are allocated per warp: pick the block size that keeps
             // the most warps resident (ties go to the larger block)
@@ -440,6 +546,8 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         r->rows_per_tile = (block / 32) * (32 / G);
     }
     if (occ < 1) return fail(QQA_EINVAL, "step kernel G=%d VPL=%d cannot run %d threads per block", G, VPL, block);
+    const int hrc = resolve_hub(r, G, VPL);
+    if (hrc) return hrc;
     c.group_lanes = G;
     c.vec_per_lane = VPL;
     c.block_threads = block;
@@ -488,10 +596,53 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
         drop_graphs(r);  // captured graphs hold the old tile pointer
     }
     if (nt) QQA_CK(cudaMemcpyAsync(r->d_tiles, tiles.data(), sizeof(Tile) * (size_t)nt, cudaMemcpyHostToDevice, st));
+    // long-row work items (one per segment) and the max-clique slots
+    std::vector<Tile> hub;
+    std::vector<int32_t> cliques;
+    for (int32_t k = 0; k < r->capacity; ++k) {
+        const SlotHost &s = r->slots[k];
+        if (!s.active) continue;
+        if (r->h_descs[k].seg_part)
+            for (int32_t q = 0; q < s.prob->nseg; ++q) hub.push_back(Tile{k, q});
+        if (s.prob->kind == QQA_MAXCLIQUE) cliques.push_back(k);
+    }
+    const int32_t nh = (int32_t)hub.size(), nc = (int32_t)cliques.size();
+    if (nh > r->hub_cap) {
+        const int32_t cap = std::max<int32_t>(nh, 2 * r->hub_cap);
+        QQA_CK(cudaStreamSynchronize(st));
+        Tile *buf = (Tile *)r->alloc.get(sizeof(Tile) * (size_t)cap, st);
+        if (!buf) return fail(QQA_ENOMEM, "long-row item list allocation failed");
+        r->alloc.put(r->d_hub_items, st);
+        r->d_hub_items = buf;
+        r->hub_cap = cap;
+        drop_graphs(r);
+    }
+    if (nh) QQA_CK(cudaMemcpyAsync(r->d_hub_items, hub.data(), sizeof(Tile) * (size_t)nh, cudaMemcpyHostToDevice, st));
+    if (nc > r->clique_cap) {
+        const int32_t cap = std::max<int32_t>(nc, 2 * r->clique_cap);
+        QQA_CK(cudaStreamSynchronize(st));
+        int32_t *buf = (int32_t *)r->alloc.get(sizeof(int32_t) * (size_t)cap, st);
+        if (!buf) return fail(QQA_ENOMEM, "clique slot list allocation failed");
+        r->alloc.put(r->d_clique_slots, st);
+        r->d_clique_slots = buf;
+        r->clique_cap = cap;
+        drop_graphs(r);
+    }
+    if (nc)
+        QQA_CK(cudaMemcpyAsync(r->d_clique_slots, cliques.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice,
+                               st));
+    // the launches of a step depend on these counts: captured graphs are redone when they change
+    const int32_t groups = r->hub_fn ? 256 / r->cfg.group_lanes : 1;
+    const int32_t hub_grid = nh == 0 ? 0 : (r->dynamic ? r->hub_max_grid : std::min(r->hub_max_grid, (nh + groups - 1) / groups));
+    if (hub_grid != r->hub_grid || nc != r->num_clique) drop_graphs(r);
+    r->hub_grid = hub_grid;
+    r->num_hub_items = nh;
+    r->num_clique = nc;
+    r->kernels_per_step = 1 + (nh ? 1 : 0) + (nc ? 1 : 0);
     // second word: the run's replica state (p^t, p^{t+1}, master, m, v) is larger
     // than most of L2, so streaming kernels mark it evict-first
     double state_bytes = 0.0;
-    const double per_elem = r->prec == kFP32 ? 16.0 : 12.0;
+    const double per_elem = r->prec == kFP32 ? 16.0 : 12.0;   // p^t, p^{t+1}, m, v (BF16: and the master)
     for (int32_t k = 0; k < r->capacity; ++k)
         if (r->slots[k].active) state_bytes += per_elem * (double)r->slots[k].n * (double)r->slots[k].S_pad;
     int dev = 0, l2 = 0;
@@ -499,25 +650,28 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     QQA_CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
     r->tile_words[0] = nt;
     r->tile_words[1] = state_bytes > 0.75 * (double)l2 ? 1 : 0;
-    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    r->tile_words[2] = nh;
+    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
     r->num_tiles = nt;
     return QQA_OK;
 }
 
 static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
-                             const qqa_allocator *alloc, void *stream, int staged_hint, qqa_run **out);
+                             const qqa_allocator *alloc, void *stream, int staged_hint, int32_t mean_deg,
+                             qqa_run **out);
 
 extern "C" int qqa_run_create_empty(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
                                     const qqa_allocator *alloc, void *stream, qqa_run **out)
 {
-    const int rc = run_create_hinted(capacity, S_max, precision, cfg, alloc, stream, 0, out);
+    const int rc = run_create_hinted(capacity, S_max, precision, cfg, alloc, stream, 0, 0, out);
     if (!rc) (*out)->dynamic = true;
     return rc;
 }
 
 static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision, const qqa_launch_config *cfg,
-                             const qqa_allocator *alloc, void *stream, int staged_hint, qqa_run **out)
+                             const qqa_allocator *alloc, void *stream, int staged_hint, int32_t mean_deg,
+                             qqa_run **out)
 {
     if (!out) return fail(QQA_EINVAL, "out is NULL");
     *out = nullptr;
@@ -529,7 +683,8 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     if (!r) return fail(QQA_ENOMEM, "host allocation failed");
     r->capacity = capacity;
     r->prec = precision;
-    r->vec = precision == QQA_FP32 ? 4 : 8;
+    r->vec = S_max == 1 ? 1 : (precision == QQA_FP32 ? 4 : 8);   // one replica: no padding lanes
+    r->mean_deg_hint = mean_deg;
     r->S_max = S_max;
     r->S_max_pad = (S_max + r->vec - 1) / r->vec * r->vec;
     r->alloc = Alloc::from(alloc);
@@ -538,7 +693,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     r->h_descs.assign(capacity, InstDesc{});
     r->slots.resize(capacity);
     r->d_descs = (InstDesc *)r->alloc.get(sizeof(InstDesc) * (size_t)capacity, st);
-    r->d_num_tiles = (int32_t *)r->alloc.get(2 * sizeof(int32_t), st);
+    r->d_num_tiles = (int32_t *)r->alloc.get(4 * sizeof(int32_t), st);
     r->d_status = (RunStatus *)r->alloc.get(sizeof(RunStatus), st);
     if (!r->d_descs || !r->d_num_tiles || !r->d_status) {
         qqa_run_destroy(r);
@@ -546,7 +701,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     }
     cudaError_t e = cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)capacity,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, 2 * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, 4 * sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_status, 0, sizeof(RunStatus), st);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -714,7 +869,17 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.master = r->prec == kBF16 ? (float *)get(elems * 4) : nullptr;
     d.m = get(elems * tb);
     d.v = get(elems * tb);
-    d.colsum = prob->kind == QQA_MAXCLIQUE ? (float *)get(3 * (size_t)s.S_pad * 4) : nullptr;
+    d.colsum = prob->kind == QQA_MAXCLIQUE ? (float *)get((size_t)s.S_pad * 4) : nullptr;
+    // long rows go to the long-row kernel (gather step kernels only)
+    const bool hubs = r->hub_fn != nullptr && prob->nlong > 0;
+    d.long_thresh = hubs ? prob->long_thresh : 0x7fffffff;
+    if (hubs) {
+        d.long_rows = prob->long_rows;
+        d.seg_ptr = prob->seg_ptr;
+        d.seg_row = prob->seg_row;
+        d.seg_part = (float *)get((size_t)prob->nseg * s.S_pad * 4);
+        d.seg_cnt = (uint32_t *)get((size_t)prob->nlong * 4);
+    }
     d.grad_dbg = nullptr;
     d.bits = (uint32_t *)get((size_t)s.n * s.W * 4);
     d.counts = (unsigned long long *)get(3 * (size_t)s.S_pad * 8);
@@ -729,7 +894,8 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.scal = (float4 *)get((size_t)kMaxChunk * sizeof(float4));
     bool ok = d.X[0] && d.X[1] && d.m && d.v && d.bits && d.counts && d.res_obj && d.res_viol && d.res_feas &&
               d.res_energy && d.res_meta && d.res_bestx && d.hist_best && d.hist_step && d.scal &&
-              (r->prec == kFP32 || d.master) && (prob->kind != QQA_MAXCLIQUE || d.colsum);
+              (r->prec == kFP32 || d.master) && (prob->kind != QQA_MAXCLIQUE || d.colsum) &&
+              (!hubs || (d.seg_part && d.seg_cnt));
     if (!ok) {
         free_slot(r, k, st);
         return fail(QQA_ENOMEM, "device allocation for instance state failed (n=%d, S=%d)", s.n, s.S);
@@ -785,13 +951,14 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     s.feas.assign(s.S, 0);
     s.energy.assign(s.S, 0.0);
     cudaError_t e = cudaMemsetAsync(d.res_meta, 0, 16, st);
+    if (e == cudaSuccess && hubs) e = cudaMemsetAsync(d.seg_cnt, 0, (size_t)prob->nlong * 4, st);
     if (e != cudaSuccess) { free_slot(r, k, st); return fail(QQA_ECUDA, "memset: %s", cudaGetErrorString(e)); }
     rc = upload_desc(r, k, st);
     if (rc) { free_slot(r, k, st); return rc; }
     launch_init(r->d_descs, k, s.n, s.S_pad, r->prec, st);
     g_launches += 1;
     if (prob->kind == QQA_MAXCLIQUE) {
-        launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+        launch_colsum(r->d_descs, nullptr, 1, k, s.S_pad, r->prec, 0, 0, st);
         g_launches += 1;
     }
     if (r->dense_N) {
@@ -846,10 +1013,11 @@ extern "C" int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stre
         if ((slot >= 0 && k != slot) || !r->slots[k].active) continue;
         const SlotHost &s = r->slots[k];
         QQA_CK(cudaMemsetAsync(r->h_descs[k].res_meta, 0, 16, st));
+        if (r->h_descs[k].seg_cnt) QQA_CK(cudaMemsetAsync(r->h_descs[k].seg_cnt, 0, (size_t)s.prob->nlong * 4, st));
         launch_init(r->d_descs, k, s.n, s.S_pad, r->prec, st);
         g_launches += 1;
         if (s.prob->kind == QQA_MAXCLIQUE) {
-            launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+            launch_colsum(r->d_descs, nullptr, 1, k, s.S_pad, r->prec, 0, 0, st);
             g_launches += 1;
         }
         if (r->dense_N) {
@@ -894,8 +1062,11 @@ extern "C" int qqa_run_create(qqa_problem *const *problems, const qqa_params *pa
     // (measured on GB300: the staged kernel does not yet beat the direct one,
     // so auto keeps the direct kernel until it does)
     const int staged_hint = (gather_rows > 2.0 * staged_rows && kAutoStaged) ? 1 : 0;
+    double nodes = 0.0;
+    for (int32_t k = 0; k < count; ++k) nodes += (double)problems[k]->n;
+    const int32_t mean_deg = (int32_t)std::min(1.0e9, std::ceil(gather_rows / std::max(nodes, 1.0)));
     qqa_run *r = nullptr;
-    int rc = run_create_hinted(count, S_max, params[0].precision, cfg, alloc, stream, staged_hint, &r);
+    int rc = run_create_hinted(count, S_max, params[0].precision, cfg, alloc, stream, staged_hint, mean_deg, &r);
     if (rc) return rc;
     for (int32_t k = 0; k < count; ++k) {
         int32_t slot = -1;
@@ -919,6 +1090,8 @@ extern "C" void qqa_run_destroy(qqa_run *r)
         if (r->slots[k].active) free_slot(r, k, 0);
     r->alloc.put(r->d_descs, 0);
     r->alloc.put(r->d_tiles, 0);
+    r->alloc.put(r->d_hub_items, 0);
+    r->alloc.put(r->d_clique_slots, 0);
     r->alloc.put(r->d_num_tiles, 0);
     r->alloc.put(r->d_status, 0);
     r->alloc.put(r->d_scratch, 0);
@@ -947,6 +1120,10 @@ static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream
         else
             r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                     r->d_status, i);
+        if (r->num_hub_items > 0)   // long rows of the same step (disjoint rows, same p^t)
+            r->hub_fn<<<r->hub_grid, 256, 0, st>>>(r->d_descs, r->d_hub_items, r->d_num_tiles + 2, r->d_status, i);
+        if (r->num_clique > 0)      // column sums of p^{t+1} for the next step's Eq. 24 term
+            launch_colsum(r->d_descs, r->d_clique_slots, r->num_clique, 0, r->S_max_pad, r->prec, i, 1, st);
     }
     launch_advance(r->d_descs, r->capacity, chunk, st);
     QQA_CK_LAUNCH("step");
@@ -994,7 +1171,7 @@ extern "C" int qqa_run_steps(qqa_run *r, int32_t nsteps, void *stream)
             int rc = launch_step_chunk(r, chunk, grid, st);
             if (rc) return rc;
         }
-        g_launches += (unsigned long long)chunk + 2;
+        g_launches += (unsigned long long)chunk * r->kernels_per_step + 2;
         for (auto &s : r->slots)
             if (s.active) s.t = std::min(s.t + chunk, s.K);
         left -= chunk;
@@ -1201,8 +1378,9 @@ extern "C" int qqa_run_set_state(qqa_run *r, int32_t k, void *stream, const floa
     launch_unpack_state(r->d_descs, k, s.n, s.S, s.S_pad, r->prec, r->d_scratch, r->d_scratch + elems,
                         r->d_scratch + 2 * elems, t, st);
     g_launches += 1;
+    if (r->h_descs[k].seg_cnt) QQA_CK(cudaMemsetAsync(r->h_descs[k].seg_cnt, 0, (size_t)s.prob->nlong * 4, st));
     if (s.prob->kind == QQA_MAXCLIQUE) {
-        launch_colsum(r->d_descs, k, s.S_pad, r->prec, st);
+        launch_colsum(r->d_descs, nullptr, 1, k, s.S_pad, r->prec, 0, 0, st);
         g_launches += 1;
     }
     if (r->dense_N) {
@@ -1229,7 +1407,7 @@ extern "C" int qqa_run_step_debug(qqa_run *r, int32_t k, void *stream, float *gr
     if (rc) return rc;
     const int32_t grid = std::min(r->max_grid, r->num_tiles);
     rc = launch_step_chunk(r, 1, grid, st);
-    g_launches += 3;
+    g_launches += (unsigned long long)r->kernels_per_step + 2;
     for (auto &sl : r->slots)
         if (sl.active) sl.t = std::min(sl.t + 1, sl.K);
     r->h_descs[k].grad_dbg = nullptr;
@@ -1240,6 +1418,16 @@ extern "C" int qqa_run_step_debug(qqa_run *r, int32_t k, void *stream, float *gr
     g_launches += 1;
     QQA_CK_LAUNCH("copy_grad");
     QQA_CK(cudaMemcpyAsync(grad, r->d_scratch + padded, elems * 4, cudaMemcpyDeviceToHost, st));
+    QQA_CK(cudaStreamSynchronize(st));
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_debug_set_status(qqa_run *r, uint64_t nonfinite, uint64_t timeouts, void *stream)
+{
+    if (!r) return fail(QQA_EINVAL, "run is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const RunStatus s{(unsigned long long)nonfinite, (unsigned long long)timeouts};
+    QQA_CK(cudaMemcpyAsync(r->d_status, &s, sizeof s, cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
     return QQA_OK;
 }

@@ -15,6 +15,23 @@ template <typename T>
 __global__ void init_kernel(const InstDesc *__restrict__ descs, int32_t slot)
 {
     const InstDesc &d = descs[slot];
+    if (d.S_pad == 1) {   // one replica per node: element 0 of each node's first quad
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+            float u[4];
+            unif4(d.seed_lo, d.seed_hi, (uint32_t)i, 0u, u);
+            if (sizeof(T) == 4) {
+                reinterpret_cast<float *>(d.X[0])[i] = u[0];
+                reinterpret_cast<float *>(d.m)[i] = 0.0f;
+                reinterpret_cast<float *>(d.v)[i] = 0.0f;
+            } else {
+                d.master[i] = u[0];
+                reinterpret_cast<__nv_bfloat16 *>(d.X[0])[i] = __float2bfloat16_rn(u[0]);
+                reinterpret_cast<__nv_bfloat16 *>(d.m)[i] = __float2bfloat16_rn(0.0f);
+                reinterpret_cast<__nv_bfloat16 *>(d.v)[i] = __float2bfloat16_rn(0.0f);
+            }
+        }
+        return;
+    }
     const int quads = d.S_pad / 4;
     const long long total = (long long)d.n * quads;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -46,7 +63,7 @@ __global__ void init_kernel(const InstDesc *__restrict__ descs, int32_t slot)
 
 void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, int32_t prec, cudaStream_t st)
 {
-    const long long total = (long long)n * (S_pad / 4);
+    const long long total = (long long)n * (S_pad == 1 ? 1 : S_pad / 4);
     const int block = 256;
     const int grid = (int)((total + block - 1) / block < 65535 ? (total + block - 1) / block : 65535);
     if (prec == kFP32) init_kernel<float><<<grid, block, 0, st>>>(descs, slot);
@@ -54,28 +71,45 @@ void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, 
 }
 
 // ---------------------------------------------------------------------------
-// Max-clique column sums sum_i p_is of the state at step t, in rotating buffer
-// t % 3, and zeroed buffer (t+1) % 3 for the next step to accumulate into.
-// One thread per replica, rows summed in order (deterministic).
+// Max-clique column sums cs_s = sum_i p_is (the Sum_i p_i term of Eq. 24) of
+// one state, always in the same order, so that clique trajectories do not
+// depend on how rows were scheduled: a 1024-thread block covers 32
+// consecutive replicas (one per lane); warp w sums rows w, w + 32, w + 64, ...
+// in order, then lane s of warp 0 adds the 32 warp sums in warp order.
+// blockIdx.y indexes the slot list (or the single slot slot0).
+// after = 1: the state p^{t+1} written by step t = d.t + r (skipped once the
+// instance has finished); after = 0: the current state p^{d.t}.
 // ---------------------------------------------------------------------------
-__global__ void colsum_kernel(const InstDesc *__restrict__ descs, int32_t slot, int32_t prec)
+__global__ void __launch_bounds__(1024) colsum_kernel(const InstDesc *__restrict__ descs,
+                                                      const int32_t *__restrict__ slots, int32_t slot0, int32_t r,
+                                                      int32_t after, int32_t prec)
 {
-    const InstDesc &d = descs[slot];
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= d.S_pad) return;
-    const int t = d.t;
+    __shared__ float part[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const InstDesc &d = descs[slots ? slots[blockIdx.y] : slot0];
+    const int t = d.t + r;
+    if (after && t >= d.K) return;                  // block-uniform
+    if ((int)blockIdx.x * 32 >= d.S_pad) return;    // block-uniform
+    const int ts = after ? t + 1 : d.t;
+    const float *src = prec == kFP32 ? reinterpret_cast<const float *>(d.X[ts & 1]) : d.master;
+    const int s = blockIdx.x * 32 + lane;
     float acc = 0.0f;
-    for (int i = 0; i < d.n; ++i) {
-        const size_t e = (size_t)i * d.S_pad + s;
-        acc += prec == kFP32 ? reinterpret_cast<const float *>(d.X[t & 1])[e] : d.master[e];
+    if (s < d.S_pad)
+        for (int i = warp; i < d.n; i += 32) acc += src[(size_t)i * d.S_pad + s];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && s < d.S_pad) {
+        float tot = 0.0f;
+        for (int w = 0; w < 32; ++w) tot += part[w][lane];
+        d.colsum[s] = tot;
     }
-    d.colsum[(t % 3) * d.S_pad + s] = acc;
-    d.colsum[((t + 1) % 3) * d.S_pad + s] = 0.0f;
 }
 
-void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st)
+void launch_colsum(const InstDesc *descs, const int32_t *slots, int32_t count, int32_t slot0, int32_t S_max_pad,
+                   int32_t prec, int32_t r, int32_t after, cudaStream_t st)
 {
-    colsum_kernel<<<(S_pad + 127) / 128, 128, 0, st>>>(descs, slot, prec);
+    const dim3 grid((unsigned)((S_max_pad + 31) / 32), (unsigned)(slots ? count : 1));
+    colsum_kernel<<<grid, 1024, 0, st>>>(descs, slots, slot0, r, after, prec);
 }
 
 // Step counters move forward once per chunk: t = min(t + nsteps, K).

@@ -1088,6 +1088,16 @@ extern "C" int qqa_color_sync(qqa_color *c)
     return QQA_OK;
 }
 
+extern "C" int qqa_color_debug_set_status(qqa_color *c, uint64_t nonfinite, uint64_t timeouts)
+{
+    if (!c) return cfail(QQA_EINVAL, "colouring handle is NULL");
+    const unsigned long long bad = nonfinite, late = timeouts;
+    COLOR_CK(cudaMemcpyAsync(c->nonfinite, &bad, sizeof bad, cudaMemcpyHostToDevice, c->st));
+    COLOR_CK(cudaMemcpyAsync(c->timeouts, &late, sizeof late, cudaMemcpyHostToDevice, c->st));
+    COLOR_CK(cudaStreamSynchronize(c->st));
+    return QQA_OK;
+}
+
 extern "C" int qqa_color_step_debug(qqa_color *c, float *grad)
 {
     if (!c) return cfail(QQA_EINVAL, "colouring handle is NULL");

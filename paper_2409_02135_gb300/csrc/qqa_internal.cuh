@@ -27,7 +27,7 @@ struct __align__(16) InstDesc {
     float *master;               // BF16 runs: FP32 master copy of p [n][S_pad]; FP32 runs: nullptr
     void *m;                     // AdamW first moment  (float or bf16) [n][S_pad]
     void *v;                     // AdamW second moment (float or bf16) [n][S_pad]
-    float *colsum;               // max-clique: column sums sum_i p_is, 3 rotating buffers [3][S_pad]
+    float *colsum;               // max-clique: column sums sum_i p_is of the current state [S_pad]
     float *grad_dbg;             // optional gradient dump [n][S_pad] (debug step only)
     // evaluation scratch and results
     uint32_t *bits;              // rounded replicas [n][W] (bit s%32 of word s/32)
@@ -48,7 +48,18 @@ struct __align__(16) InstDesc {
     const void *dense_tmaps;     // 5 TMA tensor maps: adjacency, then planes (buffer 0 hi, lo, buffer 1 hi, lo)
     uint32_t *dense_Abits;       // unit-weight graphs: adjacency bitsets [n_pad][n_pad / 32] (bit j of row i = A_ij)
     uint32_t *dense_xbits;       // rounded replicas as node bitsets [S rounded to 32][n_pad / 32]
-    int32_t n_pad, dense_N, pad4, pad5;
+    int32_t n_pad, dense_N;
+    int32_t long_thresh;         // rows with more neighbours are updated by the long-row kernel (INT32_MAX: none)
+    int32_t pad5;
+    // long rows (degree above long_thresh): their neighbour lists are summed in
+    // segments of kSegLen entries by separate work items (device copies owned by
+    // the problem; partial sums and arrival counters owned by the slot)
+    const int32_t *long_rows;    // [nlong] node index of each long row
+    const int32_t *seg_ptr;      // [nlong + 1] first segment of each long row
+    const int32_t *seg_row;      // [nseg] long row (index into long_rows) of each segment
+    float *seg_part;             // [nseg][S_pad] FP32 partial neighbour sums of the current step
+    uint32_t *seg_cnt;           // [nlong] segments of the current step done (reset to 0 by the last one)
+    const void *pad_ptr;
     // sizes
     int32_t n, S, S_pad, W;
     int32_t kind, a_ent, t, K;
@@ -63,18 +74,22 @@ struct __align__(16) InstDesc {
 // Device status word of a run.
 struct RunStatus {
     unsigned long long nonfinite;   // count of non-finite gradient / state values seen
-    unsigned long long timeouts;    // bounded waits that ran out (none in this build's kernels)
+    unsigned long long timeouts;    // bounded mbarrier waits that ran out (staged, pipelined, tensor-core kernels)
 };
 
 // Longest run of steps launched back to back (one chunk); the per-step scalar
 // table of each slot holds this many entries.
 constexpr int kMaxChunk = 64;
 
-// Tiles: (slot, first row). A block processes one tile at a time.
+// Tiles: (slot, first row). A block processes one tile at a time. The
+// long-row work items use the same record with row0 = the segment index.
 struct Tile {
     int32_t slot;
     int32_t row0;
 };
+
+// Neighbours per segment of a long row.
+constexpr int kSegLen = 32;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
@@ -386,7 +401,11 @@ void launch_init(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, 
 // dense tensor-core path: adjacency from CSR, state planes from X[t & 1]
 void launch_dense_adjacency(const InstDesc *descs, int32_t slot, int32_t n, cudaStream_t st);
 void launch_dense_planes(const InstDesc *descs, int32_t slot, int32_t n, int32_t S_pad, cudaStream_t st);
-void launch_colsum(const InstDesc *descs, int32_t slot, int32_t S_pad, int32_t prec, cudaStream_t st);
+// max-clique column sums (fixed summation order): slots = device list of
+// `count` slots (or nullptr: the one slot `slot0`); after = 1 sums the state
+// written by step d.t + r, after = 0 the current state p^{d.t}
+void launch_colsum(const InstDesc *descs, const int32_t *slots, int32_t count, int32_t slot0, int32_t S_max_pad,
+                   int32_t prec, int32_t r, int32_t after, cudaStream_t st);
 void launch_advance(InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cudaStream_t st);
 // rounding, exact costs, best replica: n_max the largest active n, total_rows the sum of active n

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
     uint64_t *mb_acc = mb_empty + kDenseStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mb_acc + 1);
     float *red = reinterpret_cast<float *>(tmem_slot + 4);   // [4][128] scratch (unused)
-    float *csum = red + 4 * 128;                              // [N] clique partial column sums
+    float *csum = red + 4 * 128;                              // [N] scratch (unused)
     float2 *rstat = reinterpret_cast<float2 *>(csum + N);     // [128] row mean, 1/STD (Eq. 10)
     float *rdeg = reinterpret_cast<float *>(rstat + 128);     // [128] weighted degree (max-cut)
 
@@ -214,13 +214,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
             const int q = warp & 3, cg = warp >> 2;
             const int rl = 32 * q + lane;
             const int col0 = cg * CPT;
-            if (c.kind == kMaxClique) {
-                for (int s2 = threadIdx.x; s2 < N; s2 += kDenseEpiWarps * 32) csum[s2] = 0.0f;
-                if (tl.row0 == 0) {
-                    float *cs_zero = d->colsum + ((t + 2) % 3) * c.S_pad;
-                    for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) cs_zero[s2] = 0.0f;
-                }
-            }
             const int gl = lane & (GE - 1), grp = lane / GE;
             const unsigned gmask = (GE == 32) ? 0xffffffffu : (((1u << GE) - 1u) << (grp * GE));
             // while the tensor cores run: row statistics of p^t and max-cut degrees
@@ -297,8 +290,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
 #pragma unroll
                         for (int e = 0; e < 4; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * 4 + e];
                     const float dsum = c.kind == kMaxCut ? rdeg[rloc] : 0.0f;
-                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, csum,
-                                              B + rloc * LD, &rstat[rloc]);
+                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, B + rloc * LD,
+                                              &rstat[rloc]);
                 }
             }
             epi_sync();
@@ -314,10 +307,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                         XTn[(size_t)s2 * n_pad + row] = hi;
                         XTn_lo[(size_t)s2 * n_pad + row] = __float2half_rn(pv - __half2float(hi));
                     }
-            }
-            if (c.kind == kMaxClique) {
-                epi_sync();
-                for (int s2 = threadIdx.x; s2 < c.S_pad; s2 += kDenseEpiWarps * 32) atomicAdd(c.cs_next + s2, csum[s2]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (!acc_ok) failed = true;

@@ -62,10 +62,9 @@ __device__ __forceinline__ float group_sum(float x, unsigned mask)
 // instance; the t-dependent ones come from the table the prepare kernel fills
 // once per chunk of steps (entry r = step t - t_chunk_start).
 struct StepCtx {
-    int t, n, S, S_pad, kind, half_pow;
+    int t, n, S, S_pad, kind, half_pow, long_thresh;
     float ent_coef, decay, step_size, inv_sqrt_bc2, lambda, alpha, noise_scale, b1, b2, adam_eps, comm_eps, inv_S;
-    const float *cs_cur;
-    float *cs_next;
+    const float *cs_cur;   // max-clique: column sums of p^t
     float *grad_dbg;
 };
 
@@ -97,34 +96,13 @@ __device__ __forceinline__ StepCtx make_ctx(const InstDesc *__restrict__ d, int 
     c.lambda = h2.z;
     c.decay = h2.w;
     c.inv_S = 1.0f / (float)c.S;
-    c.cs_cur = nullptr;
-    c.cs_next = nullptr;
+    c.long_thresh = d->long_thresh;
+    // max-clique: the column sums of p^t, formed after the previous step by the
+    // column-sum kernel (a fixed summation order, so trajectories do not depend
+    // on launch order)
+    c.cs_cur = c.kind == kMaxClique ? d->colsum : nullptr;
     c.grad_dbg = d->grad_dbg;
-    if (c.kind == kMaxClique) {
-        c.cs_cur = d->colsum + (t % 3) * c.S_pad;
-        c.cs_next = d->colsum + ((t + 1) % 3) * c.S_pad;
-    }
     return c;
-}
-
-// Clique mode: zero the rotating column-sum buffer step t+1 accumulates into
-// (once per instance, by its first tile) and the block's partial sums.
-__device__ __forceinline__ void clique_tile_begin(const InstDesc *__restrict__ d, const StepCtx &c, int row0,
-                                                  float *sh_colsum)
-{
-    if (row0 == 0) {
-        float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
-        for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) cs_zero[s] = 0.0f;
-    }
-    for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) sh_colsum[s] = 0.0f;
-    __syncthreads();
-}
-
-__device__ __forceinline__ void clique_tile_end(const StepCtx &c, const float *sh_colsum)
-{
-    __syncthreads();
-    for (int s = threadIdx.x; s < c.S_pad; s += blockDim.x) atomicAdd(c.cs_next + s, sh_colsum[s]);
-    __syncthreads();
 }
 
 // Accumulate Y += w * x for one staged or global neighbour row.
@@ -260,15 +238,6 @@ __device__ __forceinline__ void gather_row(const InstDesc *__restrict__ d, const
         }
 }
 
-// Direct gather of the whole neighbour list of `row` from global memory.
-template <typename T, int G, int VPL>
-__device__ __forceinline__ void gather_direct(const InstDesc *__restrict__ d, const T *__restrict__ Xc, int row,
-                                              int S_pad, int gl, unsigned gmask, float (&Y)[VPL][VecT<T>::N],
-                                              float &dsum)
-{
-    gather_row<T, G, VPL>(d, Xc, load_row_idx(d, row, gl), S_pad, gl, gmask, Y, dsum);
-}
-
 // The row's own data: p (FP32 master or state), the AdamW moments, and the
 // clique column sums. Loaded before the sparse product where registers allow,
 // so their latency overlaps the neighbour gathers.
@@ -348,12 +317,11 @@ __device__ __forceinline__ void load_own(const InstDesc *__restrict__ d, const S
 }
 
 // Everything after the sparse product for one row: statistics, gradient,
-// AdamW, noise, clamp, stores (and the clique partial column sums).
+// AdamW, noise, clamp, stores.
 template <typename T, int G, int VPL, bool HINT = false, typename Own = OwnRow<T, G, VPL>>
 __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const StepCtx &c, int row, int gl,
                                            unsigned gmask, const float (&Y)[VPL][VecT<T>::N], float dsum,
-                                           const Own &o, RunStatus *__restrict__ status,
-                                           float *colsum_acc, float *pn_out = nullptr,
+                                           const Own &o, RunStatus *__restrict__ status, float *pn_out = nullptr,
                                            const float2 *pre_stats = nullptr, L2Policies pol = L2Policies{0, 0})
 {
     constexpr int VEC = VecT<T>::N;
@@ -527,10 +495,6 @@ __device__ __forceinline__ void update_row(const InstDesc *__restrict__ d, const
             VecT<T>::store(reinterpret_cast<T *>(d->m) + rbase + off, M);
             VecT<T>::store(reinterpret_cast<T *>(d->v) + rbase + off, V);
         }
-        if (c.kind == kMaxClique) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) atomicAdd(colsum_acc + off + e, pn[e]);
-        }
         if (pn_out) {   // new values also go to a caller buffer (the tensor-core step's plane transpose)
 #pragma unroll
             for (int e = 0; e < VEC; ++e) pn_out[off + e] = pn[e];
@@ -550,7 +514,6 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
 {
     constexpr int VEC = VecT<T>::N;
     constexpr int ROWS_PER_WARP = 32 / G;
-    extern __shared__ float sh_colsum[];
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -565,10 +528,10 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
         const int t = d->t + r;
         if (t >= d->K) continue;   // finished instance: whole block skips (same tile)
         const StepCtx c = make_ctx(d, t, r);
-        const bool clique = (c.kind == kMaxClique);
         const int row = tl.row0 + warp * ROWS_PER_WARP + grp;
-        if (clique) clique_tile_begin(d, c, tl.row0, sh_colsum);
         if (row < c.n) {
+            const RowIdx ix = load_row_idx(d, row, gl);
+            if (ix.k1 - ix.k0 > c.long_thresh) continue;   // a long row: the long-row kernel updates it
             const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
             float Y[VPL][VEC];
 #pragma unroll
@@ -579,17 +542,16 @@ __global__ void __launch_bounds__(256) qqa_step_kernel(const InstDesc *__restric
             OwnRow<T, G, VPL> own;
             constexpr bool kPrefetch = VPL <= 2;   // own row in flight during the gather
             if (kPrefetch) load_own<T, G, VPL>(d, c, row, gl, own);
-            gather_direct<T, G, VPL>(d, Xc, row, c.S_pad, gl, gmask, Y, dsum);
+            gather_row<T, G, VPL>(d, Xc, ix, c.S_pad, gl, gmask, Y, dsum);
             if (!kPrefetch) load_own<T, G, VPL>(d, c, row, gl, own);
-            update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status, sh_colsum);
+            update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status);
         }
-        if (clique) clique_tile_end(c, sh_colsum);
     }
 }
 
 // ---------------------------------------------------------------------------
 // TMA-staged kernel. Shared memory: two mbarriers, two chunk buffers of CB
-// rows of p^t each, and the clique partial sums. Each warp owns RPW row
+// rows of p^t each, and the tile's CSR index segment. Each warp owns RPW row
 // groups, so a block covers 8 * RPW * (32 / G) rows; the block streams the
 // chunks that contain its rows' neighbours (from the smallest to the largest
 // neighbour index) and every row consumes, per chunk, the prefix of its
@@ -673,8 +635,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
     TiledSmem *hdr = reinterpret_cast<TiledSmem *>(smem_raw);
     T *buf0 = reinterpret_cast<T *>(smem_raw + 128);
     T *bufs[2] = {buf0, buf0 + buf_elems};
-    float *sh_colsum = reinterpret_cast<float *>(buf0 + 2 * (size_t)buf_elems);
-    int32_t *sidx = reinterpret_cast<int32_t *>(sh_colsum + 1024);   // colsum region holds up to 1024 floats
+    int32_t *sidx = reinterpret_cast<int32_t *>(buf0 + 2 * (size_t)buf_elems);
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -698,7 +659,6 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
         const int t = d->t + r;
         if (t >= d->K) continue;
         const StepCtx c = make_ctx(d, t, r);
-        const bool clique = (c.kind == kMaxClique);
         const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
         const int32_t *__restrict__ colp = d->col;
         const int32_t *__restrict__ wp = d->w;
@@ -706,8 +666,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
 
         // neighbour range of the block's rows -> chunks to stream
         if (threadIdx.x == 0) { hdr->lo = 0x7fffffff; hdr->hi = -1; }
-        if (clique) clique_tile_begin(d, c, tl.row0, sh_colsum);
-        else __syncthreads();
+        __syncthreads();
         int kcur[RPW], kend[RPW];
         float dsum[RPW];
         float Y[RPW][VPL][VEC];
@@ -720,6 +679,7 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
             if (row < c.n) {
                 kcur[q] = __ldg(d->row_ptr + row);
                 kend[q] = __ldg(d->row_ptr + row + 1);
+                if (kend[q] - kcur[q] > c.long_thresh) kcur[q] = kend[q];   // long row: updated by the long-row kernel
                 if (wp == nullptr) dsum[q] = (float)(kend[q] - kcur[q]);
                 if (gl == 0 && kend[q] > kcur[q]) {
                     atomicMin(&hdr->lo, __ldg(colp + kcur[q]));
@@ -835,14 +795,13 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
 #pragma unroll
         for (int q = 0; q < RPW; ++q) {
             const int row = tl.row0 + (warp * RPW + q) * GPW + grp;
-            if (row < c.n) {
+            if (row < c.n && __ldg(d->row_ptr + row + 1) - __ldg(d->row_ptr + row) <= c.long_thresh) {
                 OwnRow<T, G, VPL> own;
                 load_own<T, G, VPL>(d, c, row, gl, own);
-                update_row<T, G, VPL>(d, c, row, gl, gmask, Y[q], dsum[q], own, status, sh_colsum);
+                update_row<T, G, VPL>(d, c, row, gl, gmask, Y[q], dsum[q], own, status);
             }
         }
-        if (clique) clique_tile_end(c, sh_colsum);
-        else __syncthreads();   // hdr->lo / hi and sidx are rewritten by the next tile
+        __syncthreads();   // hdr->lo / hi and sidx are rewritten by the next tile
     }
 }
 
@@ -987,19 +946,16 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
             ctx_slot = tl.slot;
         }
         const int t = c.t;
-        const bool clique = (c.kind == kMaxClique);
-        if (clique && tl.row0 == 0) {   // zero the column sums step t+1 accumulates into
-            float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
-            for (int s = lane; s < c.S_pad; s += 32) cs_zero[s] = 0.0f;
-        }
         const int row = tl.row0 + grp;
+        // a long row is updated by the long-row kernel (its slab rows are copied all the same)
+        const bool mine = row < c.n && ix.k1 - ix.k0 <= c.long_thresh;
         float Y[VPL][VecT<T>::N];
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
             for (int e = 0; e < VecT<T>::N; ++e) Y[v][e] = 0.0f;
         float dsum = 0.0f;
-        if (row < c.n)
+        if (mine)
             gather_row<T, G, VPL, true>(d, reinterpret_cast<const T *>(d->X[t & 1]), ix, c.S_pad, gl, gmask, Y, dsum,
                                         pol.keep);
         // the next tile's first neighbour rows (one per lane of the group, up to
@@ -1030,12 +986,12 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
             return;
         }
         if (b) ++uses1; else ++uses0;
-        if (row < c.n) {
+        if (mine) {
             const unsigned char *bb = buf0 + (size_t)b * buf_bytes;
             const T *sM = reinterpret_cast<const T *>(bb + (size_t)R * c.S_pad * sizeof(float)) + (size_t)grp * c.S_pad;
             const OwnSmem<T, G, VPL> own{reinterpret_cast<const float *>(bb) + (size_t)grp * c.S_pad, sM,
                                           sM + (size_t)R * c.S_pad, gl};
-            update_row<T, G, VPL, true>(d, c, row, gl, gmask, Y, dsum, own, status, c.cs_next, nullptr, nullptr, pol);
+            update_row<T, G, VPL, true>(d, c, row, gl, gmask, Y, dsum, own, status, nullptr, nullptr, pol);
         }
         __syncwarp();   // every lane is done with buffer b
     }
@@ -1050,7 +1006,6 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
 // tracked per thread by cp.async.wait_group, so no barrier or spin-wait is
 // involved; neighbours beyond NB are gathered directly, after the prefetched
 // ones, which keeps the ascending accumulation order of the other kernels.
-// Max-clique partial column sums go straight to global memory.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
@@ -1104,6 +1059,7 @@ __global__ void __launch_bounds__(256) qqa_step_stream_kernel(const InstDesc *__
         if (x.valid) {
             x.k0 = __ldg(x.d->row_ptr + x.row);
             x.k1 = __ldg(x.d->row_ptr + x.row + 1);
+            if (x.k1 - x.k0 > x.d->long_thresh) x.valid = false;   // long row: updated by the long-row kernel
         }
         return x;
     };
@@ -1156,10 +1112,6 @@ __global__ void __launch_bounds__(256) qqa_step_stream_kernel(const InstDesc *__
         if (cur.valid) {
             const InstDesc *__restrict__ d = cur.d;
             const StepCtx c = make_ctx(d, cur.t, r);
-            if (c.kind == kMaxClique && cur.row == 0) {
-                float *cs_zero = d->colsum + ((c.t + 2) % 3) * c.S_pad;
-                for (int s2 = gl; s2 < c.S_pad; s2 += G) cs_zero[s2] = 0.0f;
-            }
             OwnRow<T, G, VPL> own;
             float Y[VPL][VEC];
             float dsum = 0.0f;
@@ -1223,9 +1175,238 @@ __global__ void __launch_bounds__(256) qqa_step_stream_kernel(const InstDesc *__
                     }
                 }
             }
-            update_row<T, G, VPL>(d, c, cur.row, gl, gmask, Y, dsum, own, status, c.cs_next);
+            update_row<T, G, VPL>(d, c, cur.row, gl, gmask, Y, dsum, own, status);
         }
         cur = nxt;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Long-row kernel. A row with more neighbours than the instance's long_thresh
+// (a hub of a scale-free graph) would keep one lane group busy for the whole
+// step while the rest of the grid idles, so its neighbour list is cut into
+// segments of kSegLen consecutive CSR entries, each a separate work item: a
+// lane group sums its segment (CSR order, as gather_row does) into an FP32
+// partial row of the slot's seg_part, and the group that completes the row's
+// last segment (an arrival counter per row; no group ever waits) adds the
+// partials in segment order, Y = ((P_0 + P_1) + P_2) + ..., and runs the row's
+// update. The order is fixed, so the result does not depend on which group
+// finishes last, and every step kernel variant leaves these rows to this one.
+// ---------------------------------------------------------------------------
+template <typename T, int G, int VPL>
+__global__ void __launch_bounds__(256) qqa_step_hub_kernel(const InstDesc *__restrict__ descs,
+                                                           const Tile *__restrict__ items,
+                                                           const int32_t *__restrict__ num_items_p,
+                                                           RunStatus *__restrict__ status, int32_t r)
+{
+    constexpr int VEC = VecT<T>::N;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int groups = (int)(blockDim.x / G);
+    const int num_items = *num_items_p;
+    const int stride = gridDim.x * groups;
+
+    for (int it = blockIdx.x * groups + (int)(threadIdx.x / G); it < num_items; it += stride) {   // group-uniform
+        const Tile itm = items[it];
+        const InstDesc *__restrict__ d = descs + itm.slot;
+        const int t = d->t + r;
+        if (t >= d->K) continue;
+        const int seg = itm.row0;
+        const int j = __ldg(d->seg_row + seg);
+        const int s0 = __ldg(d->seg_ptr + j), s1 = __ldg(d->seg_ptr + j + 1);
+        const int row = __ldg(d->long_rows + j);
+        const int rk0 = __ldg(d->row_ptr + row), rk1 = __ldg(d->row_ptr + row + 1);
+        const int S_pad = d->S_pad;
+        const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
+        RowIdx x{0, 0, 0, 0.0f};
+        x.k0 = rk0 + (seg - s0) * kSegLen;
+        x.k1 = min(x.k0 + kSegLen, rk1);
+        if (x.k0 + gl < x.k1) {
+            x.jl = __ldg(d->col + x.k0 + gl);
+            x.wl = d->w ? (float)__ldg(d->w + x.k0 + gl) : 1.0f;
+        }
+        float Y[VPL][VEC];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Y[v][e] = 0.0f;
+        float dseg = 0.0f;
+        gather_row<T, G, VPL>(d, Xc, x, S_pad, gl, gmask, Y, dseg);
+        float *part = d->seg_part + (size_t)seg * S_pad;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int off = (v * G + gl) * VEC;
+            if (off < S_pad) store_f32_vec(part + off, Y[v], VEC);
+        }
+        __threadfence();   // this lane's partial is visible before the group announces it
+        __syncwarp(gmask);
+        unsigned prev = 0;
+        if (gl == 0) prev = atomicAdd(d->seg_cnt + j, 1u);
+        prev = __shfl_sync(gmask, prev, 0, G);
+        if (prev != (unsigned)(s1 - s0 - 1)) continue;   // not the last segment of the row
+        __threadfence();
+        // the partials in segment order, read from L2 (other SMs wrote them in this launch)
+        for (int q = s0; q < s1; ++q) {
+            const float *pp = d->seg_part + (size_t)q * S_pad;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const int off = (v * G + gl) * VEC;
+                if (off < S_pad) {
+#pragma unroll
+                    for (int k = 0; k < VEC; k += 4) {
+                        const float4 a = __ldcg(reinterpret_cast<const float4 *>(pp + off + k));
+                        if (q == s0) {
+                            Y[v][k] = a.x; Y[v][k + 1] = a.y; Y[v][k + 2] = a.z; Y[v][k + 3] = a.w;
+                        } else {
+                            Y[v][k] += a.x; Y[v][k + 1] += a.y; Y[v][k + 2] += a.z; Y[v][k + 3] += a.w;
+                        }
+                    }
+                }
+            }
+        }
+        if (gl == 0) d->seg_cnt[j] = 0u;   // ready for the next step (a later launch)
+        // weighted degree of the whole row (integer weights: exact in any order)
+        float dsum = (float)(rk1 - rk0);
+        if (d->w) {
+            float ws = 0.0f;
+            for (int k = rk0 + gl; k < rk1; k += G) ws += (float)__ldg(d->w + k);
+            dsum = group_sum<G>(ws, gmask);
+        }
+        const StepCtx c = make_ctx(d, t, r);
+        OwnRow<T, G, VPL> own;
+        load_own<T, G, VPL>(d, c, row, gl, own);
+        update_row<T, G, VPL>(d, c, row, gl, gmask, Y, dsum, own, status);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One replica per node (S = 1, the paper's setting for random regular graphs):
+// the state is one value per node (p[n] in FP32, or BF16 X with the FP32
+// master; no padding lanes). A warp owns 32 consecutive rows. For the sparse
+// product, groups of L lanes take one row each, L consecutive CSR entries per
+// load (coalesced index loads); lane gl sums the entries k = k0 + gl (mod L)
+// in CSR order, then the group adds its lanes by a fixed xor tree. Lane j then
+// runs the update of row r0 + j (coalesced state accesses): with one replica
+// the communication term of Eq. 10 is zero (p equals its own mean), the rest
+// is the epilogue of the vector kernels for one element.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float load_scalar(const T *p);
+template <>
+__device__ __forceinline__ float load_scalar<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_scalar<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const unsigned short u = __ldg(reinterpret_cast<const unsigned short *>(p));
+    return __uint_as_float((uint32_t)u << 16);
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) qqa_step_scalar_kernel(const InstDesc *__restrict__ descs,
+                                                              const Tile *__restrict__ tiles,
+                                                              const int32_t *__restrict__ num_tiles_p,
+                                                              RunStatus *__restrict__ status, int32_t r)
+{
+    constexpr int RPI = 32 / L;   // rows summed at once per warp (one per lane group)
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
+    const int num_tiles = *num_tiles_p;
+
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        const InstDesc *__restrict__ d = descs + tl.slot;
+        const int t = d->t + r;
+        if (t >= d->K) continue;   // block-uniform
+        const int n = d->n;
+        const int r0 = tl.row0 + warp * 32;
+        if (r0 >= n) continue;     // warp-uniform
+        const int row = r0 + lane;
+        const bool live = row < n;
+        // this lane's row: bounds, then its own state (in flight during the gather)
+        const int kb = live ? __ldg(d->row_ptr + row) : 0;
+        const int ke = live ? __ldg(d->row_ptr + row + 1) : 0;
+        const T *__restrict__ Xc = reinterpret_cast<const T *>(d->X[t & 1]);
+        float P = 0.0f, M = 0.0f, V = 0.0f;
+        if (live) {
+            P = d->master ? d->master[row] : load_scalar<T>(Xc + row);
+            if (sizeof(T) == 4) {
+                M = reinterpret_cast<const float *>(d->m)[row];
+                V = reinterpret_cast<const float *>(d->v)[row];
+            } else {
+                M = load_scalar<__nv_bfloat16>(reinterpret_cast<const __nv_bfloat16 *>(d->m) + row);
+                V = load_scalar<__nv_bfloat16>(reinterpret_cast<const __nv_bfloat16 *>(d->v) + row);
+            }
+        }
+        const int32_t *__restrict__ colp = d->col;
+        const int32_t *__restrict__ wp = d->w;
+        float Ymine = 0.0f, Dmine = 0.0f;
+#pragma unroll 1
+        for (int it = 0; it < L; ++it) {
+            const int src = it * RPI + grp;   // the warp's row this group sums now
+            const int k0 = __shfl_sync(0xffffffffu, kb, src);
+            const int k1 = __shfl_sync(0xffffffffu, ke, src);
+            float y = 0.0f, ds = 0.0f;
+#pragma unroll 4
+            for (int k = k0 + gl; k < k1; k += L) {
+                const int jn = __ldg(colp + k);
+                const float wv = wp ? (float)__ldg(wp + k) : 1.0f;
+                y = fmaf(wv, load_scalar<T>(Xc + jn), y);
+                ds += wv;
+            }
+            y = group_sum<L>(y, gmask);
+            ds = group_sum<L>(ds, gmask);
+            // lane it * RPI + g takes the sum of group g
+            const float yv = __shfl_sync(0xffffffffu, y, (lane % RPI) * L);
+            const float dv = __shfl_sync(0xffffffffu, ds, (lane % RPI) * L);
+            if (lane / RPI == it) {
+                Ymine = yv;
+                Dmine = dv;
+            }
+        }
+        if (!live) continue;
+        const StepCtx c = make_ctx(d, t, r);
+        float g;
+        if (c.kind == kMaxClique) g = fmaf(c.lambda, (c.cs_cur[0] - 0.5f) - Ymine, -1.0f);   // Eq. 24
+        else if (c.kind == kMaxCut) g = fmaf(2.0f, Ymine, -Dmine);                            // Eq. 26
+        else g = fmaf(c.lambda, Ymine, -1.0f);                                                // Eq. 22
+        {   // annealed entropy term gamma_t (-2a) (2p - 1)^(a - 1) (Eq. 7)
+            const float u = fmaf(2.0f, P, -1.0f);
+            const float u2 = u * u;
+            float upow = u;
+            if (c.half_pow == 1) upow = u * u2;
+            else
+                for (int k = 0; k < c.half_pow; ++k) upow *= u2;
+            g = fmaf(c.ent_coef, upow, g);
+        }
+        if (c.grad_dbg) c.grad_dbg[row] = g;
+        // the Gaussian of replica 0: first Box-Muller value of node row's quad 0 (noise stream, step t)
+        const U4 rq = philox10(U4{(uint32_t)row, 0u, (uint32_t)c.t, 1u}, d->seed_lo, d->seed_hi);
+        float xi0, xi1;
+        box_muller(rq.x, rq.y, xi0, xi1);
+        const float mn = fmaf(c.b1, M, (1.0f - c.b1) * g);
+        const float vn = fmaf(c.b2, V, (1.0f - c.b2) * (g * g));
+        const float denom = fmaf(sqrt_nonneg(vn), c.inv_sqrt_bc2, c.adam_eps);
+        float q = P * c.decay;
+        q = fmaf(-c.step_size, mn * rcp_ftz(denom), q);
+        const float pn = __saturatef(fmaf(c.noise_scale, xi0, q));
+        if (!(vn <= 3.0e38f)) atomicAdd(&status->nonfinite, 1ULL);
+        T *Xn = reinterpret_cast<T *>(d->X[(t + 1) & 1]);
+        if (sizeof(T) == 4) {
+            reinterpret_cast<float *>(Xn)[row] = pn;
+            reinterpret_cast<float *>(d->m)[row] = mn;
+            reinterpret_cast<float *>(d->v)[row] = vn;
+        } else {
+            d->master[row] = pn;
+            reinterpret_cast<__nv_bfloat16 *>(Xn)[row] = __float2bfloat16_rn(pn);
+            reinterpret_cast<__nv_bfloat16 *>(d->m)[row] = __float2bfloat16_rn(mn);
+            reinterpret_cast<__nv_bfloat16 *>(d->v)[row] = __float2bfloat16_rn(vn);
+        }
     }
 }
 

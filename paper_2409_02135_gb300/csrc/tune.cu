@@ -3,7 +3,8 @@
 // The shape choices are the kernel variant (direct gather, cp.async stream
 // with 4 or 8 prefetched neighbours, TMA-staged with 2 or 4 row groups per
 // warp, pipelined with the next tile's own rows bulk-copied ahead, and for
-// FP32 runs of graphs up to 8192 nodes the tensor-core step),
+// FP32 runs of graphs up to 8192 nodes the tensor-core step; runs of one
+// replica per instance take the scalar kernel with 4 to 32 lanes per row),
 // the lanes per node row G and 16-byte vectors per lane VPL that cover
 // S_max replicas, and the block size. Each candidate runs on a temporary run
 // of the caller's instances: one warm-up chunk, then `trial_steps` steps timed
@@ -72,9 +73,13 @@ extern "C" int qqa_autotune(qqa_problem *const *problems, const qqa_params *para
         qqa_problem_info(problems[k], nullptr, &nk, nullptr);
         n_max = nk > n_max ? nk : n_max;
     }
-    if (params[0].precision == QQA_FP32 && S_max <= 256 && n_max <= 8192)   // tensor-core step (fp16 adjacency)
+    if (S_max == 1) {   // one replica per instance: the scalar kernel, lanes per row x block size
+        for (int L : {4, 8, 16, 32})
+            for (int bt : {128, 256}) cands.push_back(qqa_launch_config{0, 0, bt, 0, 1, QQA_KERNEL_SCALAR, L, 0});
+    } else if (params[0].precision == QQA_FP32 && S_max <= 256 && n_max <= 8192) {   // tensor-core step (fp16 adjacency)
         cands.push_back(qqa_launch_config{0, 0, 0, 0, 1, QQA_KERNEL_DENSE, 0, 0});
-    for (int G = 1; G <= 32; G *= 2)
+    }
+    for (int G = 1; G <= 32 && S_max > 1; G *= 2)
         for (int VPL = 1; VPL <= 8; VPL *= 2) {
             if (G * VPL < nvec || (G * VPL >= 2 * nvec && G * VPL > 1)) continue;   // cover S, at most 2x over
             for (int bt : {0, 128, 256}) cands.push_back(qqa_launch_config{G, VPL, bt, 0, 1, QQA_KERNEL_DIRECT, 0, 0});

@@ -1,10 +1,17 @@
-"""Write the oracle's mean final best objective per instance of a workload.
+"""Write the FP64 oracle's final best objective per seed for a quality set.
 
-Runs only the FP64 oracle (oracle/) on the seeded inputs of qqa_inputs; the
-output file is the target of bench.py's time-to-oracle-quality figure (the
-time until an instance's best feasible objective reaches 99% of this mean).
+Runs only the FP64 oracle (oracle/) on the seeded inputs of qqa_inputs. The
+files it writes are the targets of the GPU quality tests (best feasible
+objective per instance, mean over seeds, within 1% of the oracle's) and of
+bench.py's time-to-oracle-quality figure.
 
     python tests/golden/make_oracle_quality.py mis_er700_800 4
+    python tests/golden/make_oracle_quality.py mis_er700_800_s16
+    python tests/golden/make_oracle_quality.py maxcut_regular3_n10000
+
+Each set names a workload recipe, the instances it takes and the number of
+oracle seeds (run seed 1000 + k for seed k). The output is rewritten after
+every seed, so an interrupted run keeps what it finished and a rerun resumes.
 """
 import json
 import os
@@ -20,32 +27,80 @@ import oracle  # noqa: E402
 from qqa_inputs import workloads as W  # noqa: E402
 
 
-def workload(name):
-    if name == "mis_er700_800":
-        return W.er_mis_paper(num_graphs=16, S=128, steps=3000, base_seed=1000)
-    if name == "mis_er100":
-        return W.er_mis_small()
-    raise SystemExit(f"unknown workload {name}")
+def _er_paper():
+    return W.er_mis_paper(num_graphs=16, S=128, steps=3000, base_seed=1000)
+
+
+def _ablation(**kw):
+    """The first ER-[700-800]-shaped graph with one ablation setting changed
+    (Sec. 6: schedule length, initial gamma, communication strength)."""
+    inst = _er_paper().instances[0]
+    p = inst.params.with_(**kw)
+    tag = "_".join(f"{k}{v}" for k, v in kw.items())
+    return W.Workload(f"ablation_{tag}_{inst.name}_S{p.S}", [W.Instance(inst.kind, inst.graph, p, inst.name)])
+
+
+# name -> (workload factory, default seeds, instances taken (None = all))
+SETS = {
+    "mis_er100": (W.er_mis_small, 4, None),
+    "mis_er700_800": (_er_paper, 4, None),
+    "mis_er700_800_s16": (_er_paper, 16, 6),
+    "maxcut_regular3_n10000": (lambda: W.maxcut_large(n=10_000, family="regular3"), 16, None),
+    "maxcut_ba4_n10000": (lambda: W.maxcut_large(n=10_000, family="ba4"), 16, None),
+    "maxcut_regular3_n100000": (lambda: W.maxcut_large(n=100_000, family="regular3"), 4, None),
+    "maxcut_ba4_n100000": (lambda: W.maxcut_large(n=100_000, family="ba4"), 4, None),
+    "ablation_K100": (lambda: _ablation(steps=100), 16, None),
+    "ablation_gamma0_0": (lambda: _ablation(gamma_min=0.0), 16, None),
+    "ablation_alpha1": (lambda: _ablation(alpha_comm=1.0), 16, None),
+}
 
 
 def main():
     name = sys.argv[1] if len(sys.argv) > 1 else "mis_er700_800"
-    seeds = int(sys.argv[2]) if len(sys.argv) > 2 else 4
-    wl = workload(name)
-    out = {"workload": wl.name, "seeds": seeds, "threads": oracle.num_threads(), "instances": []}
-    for inst in wl.instances:
-        t0 = time.time()
-        bests = []
-        for seed in range(seeds):
-            r = oracle.anneal(inst.kind, inst.graph, inst.params.with_(seed=1000 + seed))
-            bests.append(int(r.eval.obj[r.eval.best]) if r.eval.best >= 0 else None)
-        ok = [b for b in bests if b is not None]
-        out["instances"].append({"name": inst.name, "n": inst.graph.n, "nnz": inst.graph.nnz,
-                                 "oracle_best": bests, "oracle_mean_best": float(np.mean(ok)) if ok else None})
-        print(inst.name, bests, f"{time.time() - t0:.1f}s", flush=True)
+    factory, seeds, take = SETS[name]
+    if len(sys.argv) > 2:
+        seeds = int(sys.argv[2])
+    wl = factory()
+    insts = wl.instances if take is None else wl.instances[:take]
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"oracle_quality_{name}.json")
-    with open(path, "w") as f:
-        json.dump(out, f, indent=1)
+    done = {}
+    if os.path.exists(path):
+        for rec in json.load(open(path)).get("instances", []):
+            done[rec["name"]] = rec
+    out = {"workload": wl.name, "set": name, "seeds": seeds, "threads": oracle.num_threads(),
+           "oracle_seed": "1000 + k", "instances": []}
+
+    def write():
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(out, f, indent=1)
+        os.replace(tmp, path)
+
+    for inst in insts:
+        p0 = inst.params
+        rec = done.get(inst.name)
+        if rec is None or "oracle_min_energy" not in rec:
+            rec = {"name": inst.name, "n": inst.graph.n, "nnz": inst.graph.nnz, "kind": inst.kind, "S": p0.S,
+                   "steps": p0.steps, "gamma_min": p0.gamma_min, "alpha_comm": p0.alpha_comm,
+                   "precision_of_recipe": "fp32" if p0.precision == W.FP32 else "bf16",
+                   "oracle_best": [], "oracle_feasible": [], "oracle_min_energy": []}
+        out["instances"].append(rec)
+        for seed in range(len(rec["oracle_best"]), seeds):
+            t0 = time.time()
+            r = oracle.anneal(inst.kind, inst.graph, p0.with_(seed=1000 + seed))
+            e = r.eval
+            rec["oracle_best"].append(int(e.obj[e.best]) if e.best >= 0 else None)
+            rec["oracle_feasible"].append(int(np.count_nonzero(e.feasible)))
+            rec["oracle_min_energy"].append(float(np.min(e.energy)))
+            ok = [b for b in rec["oracle_best"] if b is not None]
+            rec["oracle_mean_best"] = float(np.mean(ok)) if ok else None
+            rec["oracle_mean_min_energy"] = float(np.mean(rec["oracle_min_energy"]))
+            write()
+            print(name, inst.name, seed, rec["oracle_best"][-1], f"{time.time() - t0:.1f}s", flush=True)
+        ok = [b for b in rec["oracle_best"] if b is not None]
+        rec["oracle_mean_best"] = float(np.mean(ok)) if ok else None
+        rec["oracle_mean_min_energy"] = float(np.mean(rec["oracle_min_energy"])) if rec["oracle_min_energy"] else None
+    write()
     print("wrote", path)
 
 

@@ -87,6 +87,19 @@ def test_color_single_step_matches_oracle(gen, K, S):
     _check_step(g, K, p, c)
 
 
+@pytest.mark.parametrize("gen,K", [("queens:13:13", 13), ("queens:8:12", 12), ("er_large", 6)])
+def test_color_single_step_at_the_bench_replica_count(gen, K):
+    """S = 1024, the replica count the colouring benchmark runs: all eight
+    128-replica chunks of the carried partial sums of sigma, for the
+    tensor-core, shared-memory and direct neighbour sums."""
+    g = G.erdos_renyi(2000, 0.005, 9) if gen == "er_large" else _graph(gen)
+    p = Params(S=1024, steps=3000, lr=0.1, alpha_comm=0.3, seed=12, precision=FP32)
+    c = qqa.Coloring(g, K, qqa.make_params(p))
+    _check_step(g, K, p, c)
+    c.steps(30)
+    _check_step(g, K, p, c)
+
+
 def test_color_graph_replay_equals_single_launches():
     """Chunks of steps replayed from a captured CUDA graph (the step index read
     from the device counter) give the same state, bit for bit, as the same

@@ -58,11 +58,13 @@ def _check_step(kind, g, p, prec, run, slot=0, rows=None):
 
 
 # ------------------------------------------------------------ init -------
+@pytest.mark.parametrize("S", [13, 1])
 @pytest.mark.parametrize("prec", [FP32, BF16])
-def test_init_state_is_the_oracle_draw(prec):
-    """Initial p are the same Philox uniforms on both sides (exact in FP32)."""
+def test_init_state_is_the_oracle_draw(prec, S):
+    """Initial p are the same Philox uniforms on both sides (exact in FP32);
+    S = 1 uses the one-value-per-node layout."""
     g = _graph(MIS, 77, 0.1, 1)
-    p = Params(S=13, steps=10, seed=0xABCDEF12345, precision=prec)
+    p = Params(S=S, steps=10, seed=0xABCDEF12345, precision=prec)
     run = make_run(MIS, g, p)
     X, m, v, t = run.get_state(0)
     want = oracle.init_state(g.n, p.S, p.seed)
@@ -111,6 +113,47 @@ def test_single_step_matches_oracle(kind, prec, S):
     _check_step(kind, g, p, prec, run)           # t = 0 (cold moments)
     run.steps(98)
     _check_step(kind, g, p, prec, run)           # t = 99 (warm moments)
+
+
+def _interior_state(n, S, seed):
+    """A state away from the clamp (p in [0.05, 0.95]) with warm moments."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.05, 0.95, size=(n, S)).astype(np.float32)
+    m = rng.normal(0.0, 0.3, size=(n, S)).astype(np.float32)
+    v = rng.uniform(0.01, 0.5, size=(n, S)).astype(np.float32)
+    return X, m, v
+
+
+KERNEL_NAMES = {qqa.KERNEL_DIRECT: "direct", qqa.KERNEL_PIPE: "pipe", qqa.KERNEL_DENSE: "dense"}
+
+
+@pytest.mark.parametrize("kernel", [qqa.KERNEL_DIRECT, qqa.KERNEL_PIPE, qqa.KERNEL_DENSE],
+                         ids=lambda k: KERNEL_NAMES[k])
+@pytest.mark.parametrize("prec", [FP32, BF16])
+@pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
+def test_single_step_at_schedule_endpoints(kind, prec, kernel):
+    """The schedule's ends (App. C.2): the last step t = K - 1, where gamma_t =
+    gamma_max > 0 (the regime that drives p to integral points), from an interior
+    state with warm moments; and a one-step schedule K = 1 (gamma_0 = gamma_min)
+    from the initial draw. Direct, pipelined and tensor-core steps (FP32 only)."""
+    if kernel == qqa.KERNEL_DENSE and prec == BF16:
+        pytest.skip("the tensor-core step runs FP32 states")
+    g = _graph(kind, 200, 0.5 if kind == MAXCLIQUE else (0.2 if kernel == qqa.KERNEL_DENSE else 0.05), 90 + kind,
+               weighted=(kind == MAXCUT))
+    cfg = qqa.LaunchConfig(kernel=kernel)
+    gmin = -5.0 if kind == MAXCUT else -2.0
+    K = 300
+    p = Params(S=64, steps=K, alpha_comm=0.3, lr=0.3, seed=17, precision=prec, gamma_min=gmin, gamma_max=0.5)
+    run = make_run(kind, g, p, config=cfg)
+    assert run.config().kernel == kernel
+    X, m, v = _interior_state(g.n, p.S, 5 + kind)
+    run.set_state(0, X, m, v, K - 1)
+    _check_step(kind, g, p, prec, run)
+    assert run.slot_step(0) == K
+    p1 = p.with_(steps=1, seed=18)
+    run1 = make_run(kind, g, p1, config=cfg)
+    _check_step(kind, g, p1, prec, run1)
+    assert run1.slot_step(0) == 1
 
 
 @pytest.mark.parametrize("prec", [FP32, BF16])
@@ -164,7 +207,8 @@ def test_isolated_nodes_single_node_and_ragged_tiles():
                                            (FP32, 64, (16, 1, 2)), (BF16, 24, (4, 1, 4))])
 def test_staged_kernel_equals_direct_kernel(kind, prec, S, layout):
     """The TMA-staged kernel reads neighbour rows from shared memory in the same
-    ascending order as the direct gather, so states are bit-identical."""
+    ascending order as the direct gather, so states are bit-identical (max-clique
+    too: its column sums are formed in a fixed order after every step)."""
     G_, V_, R_ = layout
     g = _graph(kind, 357, 0.12, 50 + kind, weighted=(kind == MAXCUT))
     p = Params(S=S, steps=100, alpha_comm=0.3, seed=11, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
@@ -175,12 +219,9 @@ def test_staged_kernel_equals_direct_kernel(kind, prec, S, layout):
     b.steps(60)
     Xa, ma, va, _ = a.get_state(0)
     Xb, mb, vb, _ = b.get_state(0)
-    if kind == MAXCLIQUE:   # column sums are float atomics: order-dependent rounding
-        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
-    else:
-        np.testing.assert_array_equal(Xa, Xb)
-        np.testing.assert_array_equal(ma, mb)
-        np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(Xa, Xb)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(va, vb)
 
 
 @pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
@@ -205,12 +246,9 @@ def test_stream_kernel_equals_direct_kernel(kind, prec, S, layout):
     b.steps(60)
     Xa, ma, va, _ = a.get_state(0)
     Xb, mb, vb, _ = b.get_state(0)
-    if kind == MAXCLIQUE:
-        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
-    else:
-        np.testing.assert_array_equal(Xa, Xb)
-        np.testing.assert_array_equal(ma, mb)
-        np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(Xa, Xb)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(va, vb)
 
 
 @pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
@@ -235,12 +273,9 @@ def test_pipe_kernel_equals_direct_kernel(kind, prec, S, layout):
     b.steps(60)
     Xa, ma, va, _ = a.get_state(0)
     Xb, mb, vb, _ = b.get_state(0)
-    if kind == MAXCLIQUE:   # column sums are float atomics: order-dependent rounding
-        np.testing.assert_allclose(Xa, Xb, rtol=0, atol=1e-4 if prec == FP32 else 2e-2)
-    else:
-        np.testing.assert_array_equal(Xa, Xb)
-        np.testing.assert_array_equal(ma, mb)
-        np.testing.assert_array_equal(va, vb)
+    np.testing.assert_array_equal(Xa, Xb)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(va, vb)
 
 
 @pytest.mark.parametrize("prec", [FP32, BF16])
@@ -393,29 +428,31 @@ def test_each_step_of_a_trajectory_matches_oracle():
         _check_step(MAXCLIQUE, g, p, FP32, run)
 
 
-def test_steps_stop_at_K_and_checkpoint_resume_is_exact():
-    g = _graph(MIS, 100, 0.1, 2)
+@pytest.mark.parametrize("kind", [MIS, MAXCLIQUE])
+def test_steps_stop_at_K_and_checkpoint_resume_is_exact(kind):
+    g = _graph(kind, 100, 0.1 if kind == MIS else 0.5, 2)
     p = Params(S=16, steps=130, seed=8)
-    a = make_run(MIS, g, p)
+    a = make_run(kind, g, p)
     a.steps(70)
     X, m, v, t = a.get_state(0)
     a.steps(500)
     assert a.slot_step(0) == 130
-    b = make_run(MIS, g, p)
+    b = make_run(kind, g, p)
     b.set_state(0, X, m, v, t)
     b.steps(60)
     np.testing.assert_array_equal(a.get_state(0)[0], b.get_state(0)[0])
 
 
-def test_alone_equals_in_batch():
+@pytest.mark.parametrize("kind", [MIS, MAXCLIQUE])
+def test_alone_equals_in_batch(kind):
     """An instance's trajectory does not depend on what else shares the launch."""
-    gs = [_graph(MIS, 90 + 37 * k, 0.1, 30 + k) for k in range(4)]
+    gs = [_graph(kind, 90 + 37 * k, 0.1 if kind == MIS else 0.5, 30 + k) for k in range(4)]
     ps = [Params(S=32, steps=80 + 10 * k, seed=k) for k in range(4)]
     cfg = qqa.LaunchConfig(8, 1, 128)
-    batch = make_run(MIS, gs, ps, config=cfg)
+    batch = make_run(kind, gs, ps, config=cfg)
     batch.steps(100)
     for k in (0, 3):
-        alone = make_run(MIS, gs[k], ps[k], config=cfg)
+        alone = make_run(kind, gs[k], ps[k], config=cfg)
         alone.steps(100)
         np.testing.assert_array_equal(alone.get_state(0)[0], batch.get_state(k)[0])
         assert batch.slot_step(k) == min(100, ps[k].steps)

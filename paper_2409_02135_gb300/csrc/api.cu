@@ -35,8 +35,8 @@ StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
 StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
 StepFn step_dense_kernel_fp32(int N);
 using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
-PipeFn step_pipe_kernel_fp32(int G, int VPL);
-PipeFn step_pipe_kernel_bf16(int G, int VPL);
+PipeFn step_pipe_kernel_fp32(int G, int VPL, bool segs);
+PipeFn step_pipe_kernel_bf16(int G, int VPL, bool segs);
 StepFn step_hub_kernel_fp32(int G, int VPL);
 StepFn step_hub_kernel_bf16(int G, int VPL);
 StepFn step_scalar_kernel(int prec, int L);
@@ -315,6 +315,8 @@ struct qqa_run {
     int32_t dense_N = 0;              // > 0: tensor-core step (MMA width = replicas covered)
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
     PipeFn pipe_fn = nullptr;         // set when the pipelined kernel is used
+    PipeFn pipe_seg_fn = nullptr;     // its variant that also takes segment work items of long rows
+    bool seg_items = false;           // the tile list holds segment work items (pipe_seg_fn runs)
     int32_t pipe_buf = 0;             // bytes of one of its two shared-memory buffers
     int32_t chunk_rows = 0, buf_elems = 0;
     Alloc alloc;
@@ -374,6 +376,7 @@ static int resolve_scalar(qqa_run *r, qqa_launch_config c)
     r->scalar = true;
     r->tiled_fn = nullptr;
     r->pipe_fn = nullptr;
+    r->pipe_seg_fn = nullptr;
     r->hub_fn = nullptr;
     r->dense_N = 0;
     r->smem = 0;
@@ -425,6 +428,7 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     if (mode == QQA_KERNEL_AUTO) mode = QQA_KERNEL_DIRECT;
     if (mode < QQA_KERNEL_DIRECT || mode > QQA_KERNEL_PIPE) return fail(QQA_EINVAL, "unknown kernel %d", c.kernel);
     r->pipe_fn = nullptr;
+    r->pipe_seg_fn = nullptr;
     r->hub_fn = nullptr;
     if (mode == QQA_KERNEL_DENSE) {
         if (r->prec != kFP32) return fail(QQA_EINVAL, "the dense tensor-core step needs an FP32 run");
@@ -482,8 +486,9 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
         r->tiled_fn = nullptr;
         r->step_fn = nullptr;
         rpw = 0;
-        r->pipe_fn = r->prec == kFP32 ? step_pipe_kernel_fp32(G, VPL) : step_pipe_kernel_bf16(G, VPL);
-        if (!r->pipe_fn) return fail(QQA_EINVAL, "no pipelined kernel for G=%d VPL=%d", G, VPL);
+        r->pipe_fn = r->prec == kFP32 ? step_pipe_kernel_fp32(G, VPL, false) : step_pipe_kernel_bf16(G, VPL, false);
+        r->pipe_seg_fn = r->prec == kFP32 ? step_pipe_kernel_fp32(G, VPL, true) : step_pipe_kernel_bf16(G, VPL, true);
+        if (!r->pipe_fn || !r->pipe_seg_fn) return fail(QQA_EINVAL, "no pipelined kernel for G=%d VPL=%d", G, VPL);
         if (block < 32 || block > 256 || block % 32)
             return fail(QQA_EINVAL, "block_threads must be a multiple of 32 in [32, 256]");
         // every warp owns two buffers, each holding one tile's rows of p (FP32),
@@ -512,6 +517,10 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
                         r->S_max_pad, block);
         QQA_CK(cudaFuncSetAttribute(r->pipe_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
         QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->pipe_fn, block, r->smem));
+        int occ_seg = 0;   // the grid must be resident for either variant
+        QQA_CK(cudaFuncSetAttribute(r->pipe_seg_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, r->pipe_seg_fn, block, r->smem));
+        occ = std::min(occ, occ_seg);
         r->rows_per_tile = 32 / G;
     } else if (mode == QQA_KERNEL_STREAM) {
         r->tiled_fn = nullptr;
@@ -579,12 +588,23 @@ static void drop_graphs(qqa_run *r)
 static int rebuild_tiles(qqa_run *r, cudaStream_t st)
 {
     std::vector<Tile> tiles;
+    // the pipelined kernel takes the segments of long rows as work items of its
+    // own list, first (one segment per lane group of a warp); the other gather
+    // kernels leave them to the long-row kernel
+    const bool fold = r->pipe_fn != nullptr;
+    if (fold)
+        for (int32_t k = 0; k < r->capacity; ++k) {
+            const SlotHost &s = r->slots[k];
+            if (!s.active || !r->h_descs[k].hub_active) continue;
+            for (int32_t q = 0; q < s.prob->nseg; q += r->rows_per_tile) tiles.push_back(Tile{k, -(q + 1)});
+        }
     for (int32_t k = 0; k < r->capacity; ++k) {
         const SlotHost &s = r->slots[k];
         if (!s.active) continue;
         for (int32_t row0 = 0; row0 < s.n; row0 += r->rows_per_tile) tiles.push_back(Tile{k, row0});
     }
     const int32_t nt = (int32_t)tiles.size();
+    const bool seg_items = fold && !tiles.empty() && tiles.front().row0 < 0;
     if (nt > r->tile_cap) {
         int32_t cap = std::max<int32_t>(nt, 2 * r->tile_cap);
         QQA_CK(cudaStreamSynchronize(st));
@@ -602,7 +622,7 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     for (int32_t k = 0; k < r->capacity; ++k) {
         const SlotHost &s = r->slots[k];
         if (!s.active) continue;
-        if (r->h_descs[k].seg_part)
+        if (r->h_descs[k].hub_active && !fold)
             for (int32_t q = 0; q < s.prob->nseg; ++q) hub.push_back(Tile{k, q});
         if (s.prob->kind == QQA_MAXCLIQUE) cliques.push_back(k);
     }
@@ -634,7 +654,8 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     // the launches of a step depend on these counts: captured graphs are redone when they change
     const int32_t groups = r->hub_fn ? 256 / r->cfg.group_lanes : 1;
     const int32_t hub_grid = nh == 0 ? 0 : (r->dynamic ? r->hub_max_grid : std::min(r->hub_max_grid, (nh + groups - 1) / groups));
-    if (hub_grid != r->hub_grid || nc != r->num_clique) drop_graphs(r);
+    if (hub_grid != r->hub_grid || nc != r->num_clique || seg_items != r->seg_items) drop_graphs(r);
+    r->seg_items = seg_items;
     r->hub_grid = hub_grid;
     r->num_hub_items = nh;
     r->num_clique = nc;
@@ -870,13 +891,17 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.m = get(elems * tb);
     d.v = get(elems * tb);
     d.colsum = prob->kind == QQA_MAXCLIQUE ? (float *)get((size_t)s.S_pad * 4) : nullptr;
-    // long rows go to the long-row kernel (gather step kernels only)
+    // long rows: the evaluation always splits them; the gather step kernels
+    // leave them to segment work items (partial sums and counters per slot)
     const bool hubs = r->hub_fn != nullptr && prob->nlong > 0;
-    d.long_thresh = hubs ? prob->long_thresh : 0x7fffffff;
+    d.long_thresh = prob->nlong > 0 ? prob->long_thresh : 0x7fffffff;
+    d.hub_active = hubs ? 1 : 0;
+    d.nlong = prob->nlong;
+    d.nseg = prob->nseg;
+    d.long_rows = prob->long_rows;
+    d.seg_ptr = prob->seg_ptr;
+    d.seg_row = prob->seg_row;
     if (hubs) {
-        d.long_rows = prob->long_rows;
-        d.seg_ptr = prob->seg_ptr;
-        d.seg_row = prob->seg_row;
         d.seg_part = (float *)get((size_t)prob->nseg * s.S_pad * 4);
         d.seg_cnt = (uint32_t *)get((size_t)prob->nlong * 4);
     }
@@ -1115,7 +1140,8 @@ static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream
             r->tiled_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                      r->d_status, i, r->chunk_rows, r->buf_elems);
         else if (r->pipe_fn)
-            r->pipe_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
+            (r->seg_items ? r->pipe_seg_fn : r->pipe_fn)<<<grid, r->cfg.block_threads, r->smem, st>>>(
+                r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                     r->d_status, i, r->pipe_buf);
         else
             r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
@@ -1185,14 +1211,15 @@ extern "C" int qqa_run_eval(qqa_run *r, void *stream)
     if (!r) return fail(QQA_EINVAL, "run is NULL");
     if (r->num_tiles == 0) return QQA_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    int32_t n_max = 0;
+    int32_t n_max = 0, seg_max = 0;
     int64_t total_rows = 0;
     for (const auto &s : r->slots)
         if (s.active) {
             n_max = std::max(n_max, s.n);
+            seg_max = std::max(seg_max, s.prob->nseg);
             total_rows += s.n;
         }
-    launch_eval(r->d_descs, r->capacity, n_max, total_rows, r->S_max_pad, r->prec, r->dense_N > 0, st);
+    launch_eval(r->d_descs, r->capacity, n_max, total_rows, r->S_max_pad, r->prec, r->dense_N > 0, seg_max, st);
     g_launches += r->dense_N > 0 ? 7 : 5;
     QQA_CK_LAUNCH("eval");
     for (auto &s : r->slots)

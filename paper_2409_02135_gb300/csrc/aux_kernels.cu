@@ -199,15 +199,30 @@ __global__ void eval_bits_kernel(const InstDesc *__restrict__ descs, int32_t row
 // Threads sharing a replica split the chunk's rows; each walks its rows'
 // neighbour lists eight entries at a time with the index and bit-word loads
 // of a batch in flight together. Partial counts are combined in shared
-// memory, then added to the slot's counters.
+// memory, then added to the slot's counters. The neighbour lists of long rows
+// are walked by blocks of their own, one per 32-entry segment (blocks past the
+// slot's row chunks), so a hub does not hold up the evaluation; the counts are
+// integers, so the split changes no result.
 __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, int32_t rows)
 {
     extern __shared__ long long sh_cnt[];   // [3][S_pad32]
     const InstDesc &d = descs[blockIdx.y];
     if (!needs_eval(d) || d.dense_Abits) return;   // bitset slots are counted by eval_count_bits_kernel
-    const int r0 = blockIdx.x * rows;
-    if (r0 >= d.n) return;   // block-uniform
-    const int row_end = min(r0 + rows, d.n);
+    const int nchunks = (d.n + rows - 1) / rows;
+    const bool seg_block = (int)blockIdx.x >= nchunks;
+    int r0, row_end, ks0 = 0, ks1 = 0;
+    if (!seg_block) {
+        r0 = blockIdx.x * rows;
+        row_end = min(r0 + rows, d.n);
+    } else {
+        const int q = blockIdx.x - nchunks;
+        if (q >= d.nseg) return;   // block-uniform
+        const int jl = d.seg_row[q];
+        r0 = d.long_rows[jl];
+        row_end = r0 + 1;
+        ks0 = d.row_ptr[r0] + (q - d.seg_ptr[jl]) * kSegLen;
+        ks1 = min(ks0 + kSegLen, d.row_ptr[r0 + 1]);
+    }
     const int S32 = (d.S + 31) & ~31;
     for (int k = threadIdx.x; k < 3 * S32; k += blockDim.x) sh_cnt[k] = 0;
     __syncthreads();
@@ -224,9 +239,15 @@ __global__ void eval_count_kernel(const InstDesc *__restrict__ descs, int32_t ro
         long long size = 0, inside = 0, cut = 0;
         for (int i = r0 + part; i < row_end; i += splits) {
             const unsigned xi = (bits[(size_t)i * d.W + w] >> b) & 1u;
-            size += xi;
-            const int k1 = d.row_ptr[i + 1];
-            for (int k = d.row_ptr[i]; k < k1; k += 8) {
+            int kb = d.row_ptr[i], k1 = d.row_ptr[i + 1];
+            if (seg_block) {
+                kb = ks0;
+                k1 = ks1;
+            } else {
+                size += xi;
+                if (d.long_rows && k1 - kb > d.long_thresh) continue;   // walked by its segment blocks
+            }
+            for (int k = kb; k < k1; k += 8) {
                 int j[8];
                 unsigned word[8];
 #pragma unroll
@@ -405,7 +426,7 @@ __global__ void eval_mark_kernel(InstDesc *__restrict__ descs, int32_t capacity)
 }
 
 void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
-                 int32_t prec, bool dense, cudaStream_t st)
+                 int32_t prec, bool dense, int32_t seg_max, cudaStream_t st)
 {
     // rows per counting chunk: a multiple of 8, small enough for about four
     // waves of 256-thread blocks (8 per SM) over the whole run
@@ -416,7 +437,8 @@ void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t
     const dim3 grid(std::max(1, (n_max + rows - 1) / rows), capacity);
     eval_bits_kernel<<<grid, 256, 0, st>>>(descs, rows, prec);
     const int S32 = (S_max_pad + 31) & ~31;
-    eval_count_kernel<<<grid, 256, 3 * S32 * sizeof(long long), st>>>(descs, rows);
+    const dim3 grid_c(grid.x + (unsigned)seg_max, capacity);   // row chunks, then long-row segments
+    eval_count_kernel<<<grid_c, 256, 3 * S32 * sizeof(long long), st>>>(descs, rows);
     if (dense) {   // unit-weight slots of the tensor-core step: costs by popcount over bitsets
         const int nw = (n_max + 127) / 128 * 4;   // 32-node words of the largest n_pad
         const int W = S32 / 32;

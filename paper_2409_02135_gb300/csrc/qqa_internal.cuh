@@ -49,17 +49,18 @@ struct __align__(16) InstDesc {
     uint32_t *dense_Abits;       // unit-weight graphs: adjacency bitsets [n_pad][n_pad / 32] (bit j of row i = A_ij)
     uint32_t *dense_xbits;       // rounded replicas as node bitsets [S rounded to 32][n_pad / 32]
     int32_t n_pad, dense_N;
-    int32_t long_thresh;         // rows with more neighbours are updated by the long-row kernel (INT32_MAX: none)
-    int32_t pad5;
-    // long rows (degree above long_thresh): their neighbour lists are summed in
-    // segments of kSegLen entries by separate work items (device copies owned by
-    // the problem; partial sums and arrival counters owned by the slot)
+    int32_t long_thresh;         // rows with more neighbours than this are long (INT32_MAX: none)
+    int32_t hub_active;          // 1: the step kernels leave long rows to the segment work items
+    // long rows: their neighbour lists are summed in segments of kSegLen entries
+    // by separate work items (tables owned by the problem; the evaluation splits
+    // them the same way; partial sums and arrival counters owned by the slot,
+    // present when hub_active)
     const int32_t *long_rows;    // [nlong] node index of each long row
     const int32_t *seg_ptr;      // [nlong + 1] first segment of each long row
     const int32_t *seg_row;      // [nseg] long row (index into long_rows) of each segment
     float *seg_part;             // [nseg][S_pad] FP32 partial neighbour sums of the current step
     uint32_t *seg_cnt;           // [nlong] segments of the current step done (reset to 0 by the last one)
-    const void *pad_ptr;
+    int32_t nlong, nseg;
     // sizes
     int32_t n, S, S_pad, W;
     int32_t kind, a_ent, t, K;
@@ -90,6 +91,10 @@ struct Tile {
 
 // Neighbours per segment of a long row.
 constexpr int kSegLen = 32;
+
+// A tile record with row0 < 0 stands for segment work items of long rows (the
+// pipelined kernel's list): segments -row0 - 1, ..., one per lane group.
+__host__ __device__ __forceinline__ int32_t seg_item_first(int32_t row0) { return -row0 - 1; }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
@@ -411,7 +416,7 @@ void launch_prepare(const InstDesc *descs, int32_t capacity, int32_t nsteps, cud
 // rounding, exact costs, best replica: n_max the largest active n, total_rows the sum of active n
 // dense: the run keeps the tensor-core step's adjacency bitsets (costs by popcount)
 void launch_eval(const InstDesc *descs, int32_t capacity, int32_t n_max, int64_t total_rows, int32_t S_max_pad,
-                 int32_t prec, bool dense, cudaStream_t st);
+                 int32_t prec, bool dense, int32_t seg_max, cudaStream_t st);
 void launch_pack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,
                        int32_t which, float *dst, cudaStream_t st);
 void launch_unpack_state(const InstDesc *descs, int32_t slot, int32_t n, int32_t S, int32_t S_pad, int32_t prec,

@@ -96,7 +96,7 @@ __device__ __forceinline__ StepCtx make_ctx(const InstDesc *__restrict__ d, int 
     c.lambda = h2.z;
     c.decay = h2.w;
     c.inv_S = 1.0f / (float)c.S;
-    c.long_thresh = d->long_thresh;
+    c.long_thresh = d->hub_active ? d->long_thresh : 0x7fffffff;
     // max-clique: the column sums of p^t, formed after the previous step by the
     // column-sum kernel (a fixed summation order, so trajectories do not depend
     // on launch order)
@@ -604,8 +604,10 @@ __device__ __forceinline__ void tma_bulk_load_hint(void *dst, const void *src, u
 }
 
 // Wait for phase `parity` of mbar with a clock limit; false if it ran out.
+// (The clock is read only once the phase is found incomplete.)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity)
 {
+    if (mbar_try_wait(mbar, parity)) return true;
     const long long start = clock64();
     while (!mbar_try_wait(mbar, parity)) {
         if (clock64() - start > (1LL << 31)) return false;   // ~1 s at 2 GHz
@@ -816,6 +818,64 @@ __global__ void __launch_bounds__(256) qqa_step_tiled_kernel(const InstDesc *__r
 // no block-wide barriers the warps of an SM drift apart, so one warp's gather
 // latency is covered by the others' epilogues.
 // ---------------------------------------------------------------------------
+// One lane group's segment partial P (FP32) of a long row: store it, and
+// announce it on the row's arrival counter. The group that brings the count to
+// the row's number of segments sums the partials in segment order into Y
+// (Y = ((P_0 + P_1) + P_2) + ...), resets the counter for the next step and
+// returns true; every other group returns false. No group waits for another.
+template <typename T, int G, int VPL>
+__device__ __forceinline__ bool seg_arrive(const InstDesc *__restrict__ d, int seg, int j, int s0, int s1, int gl,
+                                           unsigned gmask, float (&Y)[VPL][VecT<T>::N])
+{
+    constexpr int VEC = VecT<T>::N;
+    const int S_pad = d->S_pad;
+    float *part = d->seg_part + (size_t)seg * S_pad;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int off = (v * G + gl) * VEC;
+        if (off < S_pad) store_f32_vec(part + off, Y[v], VEC);
+    }
+    __threadfence();   // this lane's partial is visible before the group announces it
+    __syncwarp(gmask);
+    unsigned prev = 0;
+    if (gl == 0) prev = atomicAdd(d->seg_cnt + j, 1u);
+    prev = __shfl_sync(gmask, prev, 0, G);
+    if (prev != (unsigned)(s1 - s0 - 1)) return false;   // not the last segment of the row
+    __threadfence();
+    // the partials in segment order, read from L2 (other SMs wrote them in this launch)
+    for (int q = s0; q < s1; ++q) {
+        const float *pp = d->seg_part + (size_t)q * S_pad;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int off = (v * G + gl) * VEC;
+            if (off < S_pad) {
+#pragma unroll
+                for (int k = 0; k < VEC; k += 4) {
+                    const float4 a = __ldcg(reinterpret_cast<const float4 *>(pp + off + k));
+                    if (q == s0) {
+                        Y[v][k] = a.x; Y[v][k + 1] = a.y; Y[v][k + 2] = a.z; Y[v][k + 3] = a.w;
+                    } else {
+                        Y[v][k] += a.x; Y[v][k + 1] += a.y; Y[v][k + 2] += a.z; Y[v][k + 3] += a.w;
+                    }
+                }
+            }
+        }
+    }
+    if (gl == 0) d->seg_cnt[j] = 0u;   // ready for the next step (a later launch)
+    return true;
+}
+
+// Weighted degree sum_k w_k of a row (its neighbour count when unweighted);
+// integer weights, so the sum is exact in any order.
+template <int G>
+__device__ __forceinline__ float row_weight_sum(const InstDesc *__restrict__ d, int k0, int k1, int gl, unsigned gmask)
+{
+    if (!d->w) return (float)(k1 - k0);
+    float ws = 0.0f;
+    for (int k = k0 + gl; k < k1; k += G) ws += (float)__ldg(d->w + k);
+    return group_sum<G>(ws, gmask);
+}
+
 template <typename T, int G, int VPL>
 __device__ __forceinline__ void load_own_smem(const unsigned char *buf, int R, int S_pad, int lrow, int gl,
                                               OwnRow<T, G, VPL> &o)
@@ -843,7 +903,9 @@ __device__ __forceinline__ void load_own_smem(const unsigned char *buf, int R, i
     }
 }
 
-template <typename T, int G, int VPL>
+// SEGS: the tile list may hold segment work items of long rows (runs without
+// long rows take the variant without that path).
+template <typename T, int G, int VPL, bool SEGS>
 __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__restrict__ descs,
                                                             const Tile *__restrict__ tiles,
                                                             const int32_t *__restrict__ num_tiles_p,
@@ -876,61 +938,101 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     __syncwarp();
 
     // Whole warp: start the copies of tile tl's slabs into buffer b (nothing for
-    // a finished instance, whose tile the warp skips); lanes 0, 1, 2 issue the
-    // copies of p, m and v side by side. Returns whether it did.
+    // a finished instance, whose tile the warp skips, or for segment work);
+    // lanes 0, 1, 2 issue the copies of p, m and v side by side. Returns
+    // whether it did.
+    // The step context of the instance of the previous tile (most consecutive
+    // tiles of a warp belong to the same instance), with what the next tile's
+    // copies, indices and prefetches need from it: this lane's copy source
+    // (lanes 0, 1, 2: p, m, v), its cache policy and the gather base p^t, so
+    // that a tile of the same instance reads nothing from its descriptor.
+    const unsigned char *my_slab = nullptr;
+    const void *xcur = nullptr;
+    uint64_t my_hint = 0;
+    int ctx_slot = -1;
+    StepCtx c{};
     auto issue = [&](const Tile &tl, int b) -> bool {
-        const InstDesc *__restrict__ d = descs + tl.slot;
-        const int t = d->t + r;
-        if (t >= d->K) return false;
-        const int rows = min(R, d->n - tl.row0);
-        const size_t e0 = (size_t)tl.row0 * d->S_pad;
-        const uint32_t pbytes = (uint32_t)(rows * d->S_pad * sizeof(float));
-        const uint32_t sbytes = (uint32_t)(rows * d->S_pad * sizeof(T));
+        if (SEGS && tl.row0 < 0) return false;   // segments of long rows: no slabs
+        int S_pad, n;
+        const unsigned char *base;
+        uint64_t hint;
+        if (tl.slot == ctx_slot) {
+            S_pad = c.S_pad;
+            n = c.n;
+            base = my_slab;
+            hint = my_hint;
+        } else {
+            const InstDesc *__restrict__ d = descs + tl.slot;
+            const int t = d->t + r;
+            if (t >= d->K) return false;
+            S_pad = d->S_pad;
+            n = d->n;
+            if (lane == 0) base = reinterpret_cast<const unsigned char *>(d->master ? d->master : reinterpret_cast<const float *>(d->X[t & 1]));
+            else base = reinterpret_cast<const unsigned char *>(lane == 1 ? d->m : d->v);
+            hint = (lane == 0 && !d->master) ? pol.keep : pol.stream;
+        }
+        const int rows = min(R, n - tl.row0);
+        const size_t e0 = (size_t)tl.row0 * S_pad;
+        const uint32_t pbytes = (uint32_t)(rows * S_pad * sizeof(float));
+        const uint32_t sbytes = (uint32_t)(rows * S_pad * sizeof(T));
         if (lane == 0) mbar_arrive_expect_tx(&mbar[b], pbytes + 2 * sbytes);
         __syncwarp();   // the expected bytes are registered before any copy can land
         if (lane < 3) {
-            const size_t mofs = (size_t)R * d->S_pad * sizeof(float);
-            const size_t vofs = mofs + (size_t)R * d->S_pad * sizeof(T);
+            const size_t mofs = (size_t)R * S_pad * sizeof(float);
+            const size_t vofs = mofs + (size_t)R * S_pad * sizeof(T);
             unsigned char *dst = buf0 + (size_t)b * buf_bytes + (lane == 0 ? 0 : (lane == 1 ? mofs : vofs));
-            const void *src;
-            if (lane == 0)
-                src = d->master ? d->master + e0 : reinterpret_cast<const float *>(d->X[t & 1]) + e0;
-            else
-                src = reinterpret_cast<const T *>(lane == 1 ? d->m : d->v) + e0;
-            // (FP32 runs read p^t itself here; it is gathered too, so it is kept)
-            const uint64_t hint = (lane == 0 && !d->master) ? pol.keep : pol.stream;
+            const void *src = base + e0 * (lane == 0 ? sizeof(float) : sizeof(T));
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tma_bulk_load_hint(dst, src, lane == 0 ? pbytes : sbytes, &mbar[b], hint);
         }
         return true;
+    };
+    // with one vector per lane there are registers to spare for the context
+    // slot's CSR pointers too (measured: they help there and cost at VPL = 2)
+    constexpr bool kCacheCsr = VPL == 1;
+    const int32_t *rp_c = nullptr, *col_c = nullptr, *w_c = nullptr;
+    auto tile_idx = [&](const Tile &tl) -> RowIdx {
+        if (SEGS && tl.row0 < 0) return RowIdx{0, 0, 0, 0.0f};
+        if (!kCacheCsr || tl.slot != ctx_slot) return load_row_idx(descs + tl.slot, tl.row0 + grp, gl);
+        const int row = tl.row0 + grp;
+        RowIdx x{0, 0, 0, 0.0f};
+        if (row < c.n) {
+            x.k0 = __ldg(rp_c + row);
+            x.k1 = __ldg(rp_c + row + 1);
+            if (x.k0 + gl < x.k1) {
+                x.jl = __ldg(col_c + x.k0 + gl);
+                x.wl = w_c ? (float)__ldg(w_c + x.k0 + gl) : 1.0f;
+            }
+        }
+        return x;
     };
 
     // Software pipeline over the warp's tiles: tile records are fetched two
     // tiles ahead, the row bounds and first neighbour indices one tile ahead,
     // the slabs one tile ahead, and the next tile's first neighbour rows are
     // prefetched into L1 during this tile's update, so little of a tile's
-    // memory latency is exposed.
+    // memory latency is exposed. Segment work items of long rows (listed
+    // first) take the long-row kernel's steps inside this loop: each lane group
+    // sums one segment into its partial row, and the group that completes a
+    // row copies the row's own state into the warp's free buffer and updates
+    // it like any other row.
     const Tile none{0, 0};
     Tile tl_cur = first < num_tiles ? tiles[first] : none;
     Tile tl_nxt = first + W < num_tiles ? tiles[first + W] : none;
-    RowIdx ix_cur = first < num_tiles ? load_row_idx(descs + tl_cur.slot, tl_cur.row0 + grp, gl) : RowIdx{0, 0, 0, 0.0f};
+    RowIdx ix_cur = first < num_tiles ? tile_idx(tl_cur) : RowIdx{0, 0, 0, 0.0f};
 
     // completed phases of each buffer's barrier, and whether a copy is in
     // flight into the buffer not being read (warp-uniform)
     uint32_t uses0 = 0u, uses1 = 0u;
     bool next_pending = false;
     int b = 0;
-    // the step context of the instance of the previous tile (most consecutive
-    // tiles of a warp belong to the same instance)
-    int ctx_slot = -1;
-    StepCtx c{};
     if (first < num_tiles) issue(tl_cur, 0);
     for (int tile = first; tile < num_tiles; tile += W, b ^= 1) {
         const bool has_next = tile + W < num_tiles;
         // buffer b^1 was last read in the previous iteration, which ended in __syncwarp
         next_pending = has_next && issue(tl_nxt, b ^ 1);
         RowIdx ix_nxt{0, 0, 0, 0.0f};
-        if (has_next) ix_nxt = load_row_idx(descs + tl_nxt.slot, tl_nxt.row0 + grp, gl);
+        if (has_next) ix_nxt = tile_idx(tl_nxt);
         const Tile tl_nn = tile + 2 * W < num_tiles ? tiles[tile + 2 * W] : none;
 
         const Tile tl = tl_cur;
@@ -944,50 +1046,112 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
             if (t >= d->K) continue;   // finished instance: no copy was issued, nothing is read
             c = make_ctx(d, t, r);
             ctx_slot = tl.slot;
+            xcur = d->X[t & 1];
+            if (lane == 0) my_slab = reinterpret_cast<const unsigned char *>(d->master ? d->master : reinterpret_cast<const float *>(d->X[t & 1]));
+            else my_slab = reinterpret_cast<const unsigned char *>(lane == 1 ? d->m : d->v);
+            my_hint = (lane == 0 && !d->master) ? pol.keep : pol.stream;
+            if (kCacheCsr) {
+                rp_c = d->row_ptr;
+                col_c = d->col;
+                w_c = d->w;
+            }
         }
-        const int t = c.t;
-        const int row = tl.row0 + grp;
-        // a long row is updated by the long-row kernel (its slab rows are copied all the same)
-        const bool mine = row < c.n && ix.k1 - ix.k0 <= c.long_thresh;
+        const T *__restrict__ Xc = reinterpret_cast<const T *>(xcur);
+        unsigned char *const bb = buf0 + (size_t)b * buf_bytes;
+        const bool segs = SEGS && tl.row0 < 0;
         float Y[VPL][VecT<T>::N];
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
             for (int e = 0; e < VecT<T>::N; ++e) Y[v][e] = 0.0f;
         float dsum = 0.0f;
-        if (mine)
-            gather_row<T, G, VPL, true>(d, reinterpret_cast<const T *>(d->X[t & 1]), ix, c.S_pad, gl, gmask, Y, dsum,
-                                        pol.keep);
+        int row = tl.row0 + grp;
+        bool mine = false;
+        if (!segs) {
+            // a long row is updated by its segment items (its slab rows are copied all the same)
+            mine = row < c.n && ix.k1 - ix.k0 <= c.long_thresh;
+            if (mine) gather_row<T, G, VPL, true>(d, Xc, ix, c.S_pad, gl, gmask, Y, dsum, pol.keep);
+        } else {
+            const int seg = seg_item_first(tl.row0) + grp;
+            if (seg < d->nseg) {   // group-uniform
+                const int j = __ldg(d->seg_row + seg);
+                const int s0 = __ldg(d->seg_ptr + j), s1 = __ldg(d->seg_ptr + j + 1);
+                row = __ldg(d->long_rows + j);
+                const int rk0 = __ldg(d->row_ptr + row), rk1 = __ldg(d->row_ptr + row + 1);
+                RowIdx x{0, 0, 0, 0.0f};
+                x.k0 = rk0 + (seg - s0) * kSegLen;
+                x.k1 = min(x.k0 + kSegLen, rk1);
+                if (x.k0 + gl < x.k1) {
+                    x.jl = __ldg(d->col + x.k0 + gl);
+                    x.wl = d->w ? (float)__ldg(d->w + x.k0 + gl) : 1.0f;
+                }
+                gather_row<T, G, VPL, true>(d, Xc, x, c.S_pad, gl, gmask, Y, dsum, pol.keep);
+                mine = seg_arrive<T, G, VPL>(d, seg, j, s0, s1, gl, gmask, Y);
+                if (mine) {
+                    dsum = row_weight_sum<G>(d, rk0, rk1, gl, gmask);
+                    // the row's own p (FP32; the master in BF16 runs), m and v into
+                    // this group's row of the free buffer, where the update reads them
+                    constexpr int VEC = VecT<T>::N;
+                    const size_t rb = (size_t)row * c.S_pad;
+                    const float *gp = d->master ? d->master + rb : reinterpret_cast<const float *>(Xc) + rb;
+                    float *sp = reinterpret_cast<float *>(bb) + (size_t)grp * c.S_pad;
+                    T *sm = reinterpret_cast<T *>(bb + (size_t)R * c.S_pad * sizeof(float)) + (size_t)grp * c.S_pad;
+                    T *sv = sm + (size_t)R * c.S_pad;
+#pragma unroll
+                    for (int v = 0; v < VPL; ++v) {
+                        const int off = (v * G + gl) * VEC;
+                        if (off < c.S_pad) {
+#pragma unroll
+                            for (int k = 0; k < VEC; k += 4)
+                                *reinterpret_cast<float4 *>(sp + off + k) = *reinterpret_cast<const float4 *>(gp + off + k);
+                            *reinterpret_cast<uint4 *>(sm + off) =
+                                *reinterpret_cast<const uint4 *>(reinterpret_cast<const T *>(d->m) + rb + off);
+                            *reinterpret_cast<uint4 *>(sv + off) =
+                                *reinterpret_cast<const uint4 *>(reinterpret_cast<const T *>(d->v) + rb + off);
+                        }
+                    }
+                    __syncwarp(gmask);
+                }
+            }
+        }
         // the next tile's first neighbour rows (one per lane of the group, up to
         // G of them) are pulled from L2 into L1 while this tile is updated, so
         // its gather finds them there; its row bounds and first indices were
         // requested before this tile's gather
         if (has_next && ix_cur.k0 + gl < ix_cur.k1) {
-            const InstDesc *__restrict__ dn = descs + tl_cur.slot;
-            const int tn = dn->t + r;
-            if (tn < dn->K) {
-                const char *src = reinterpret_cast<const char *>(reinterpret_cast<const T *>(dn->X[tn & 1]) +
-                                                                 (size_t)ix_cur.jl * dn->S_pad);
-                const int bytes = dn->S_pad * (int)sizeof(T);
+            const void *xn = xcur;
+            int spn = c.S_pad;
+            bool live = true;
+            if (tl_cur.slot != ctx_slot) {
+                const InstDesc *__restrict__ dn = descs + tl_cur.slot;
+                const int tn = dn->t + r;
+                live = tn < dn->K;
+                xn = dn->X[tn & 1];
+                spn = dn->S_pad;
+            }
+            if (live) {
+                const char *src = reinterpret_cast<const char *>(reinterpret_cast<const T *>(xn) + (size_t)ix_cur.jl * spn);
+                const int bytes = spn * (int)sizeof(T);
                 for (int o = 0; o < bytes; o += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(src + o));
             }
         }
-        const uint32_t parity = (b ? uses1 : uses0) & 1u;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[b], parity));
-        if (!ok) {
-            // the slabs did not arrive in time: flag it, let every copy still in
-            // flight land (bounded), and leave without touching the state
-            if (lane == 0) {
-                atomicAdd(&status->timeouts, 1ULL);
-                if (next_pending) mbar_wait_bounded(&mbar[b ^ 1], (b ? uses0 : uses1) & 1u);
-                mbar_wait_bounded(&mbar[b], parity);
+        if (!segs) {   // the slabs of this tile (segment items copied none)
+            const uint32_t parity = (b ? uses1 : uses0) & 1u;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mbar[b], parity));
+            if (!ok) {
+                // the slabs did not arrive in time: flag it, let every copy still in
+                // flight land (bounded), and leave without touching the state
+                if (lane == 0) {
+                    atomicAdd(&status->timeouts, 1ULL);
+                    if (next_pending) mbar_wait_bounded(&mbar[b ^ 1], (b ? uses0 : uses1) & 1u);
+                    mbar_wait_bounded(&mbar[b], parity);
+                }
+                __syncwarp();
+                return;
             }
-            __syncwarp();
-            return;
+            if (b) ++uses1; else ++uses0;
         }
-        if (b) ++uses1; else ++uses0;
         if (mine) {
-            const unsigned char *bb = buf0 + (size_t)b * buf_bytes;
             const T *sM = reinterpret_cast<const T *>(bb + (size_t)R * c.S_pad * sizeof(float)) + (size_t)grp * c.S_pad;
             const OwnSmem<T, G, VPL> own{reinterpret_cast<const float *>(bb) + (size_t)grp * c.S_pad, sM,
                                           sM + (size_t)R * c.S_pad, gl};
@@ -1059,7 +1223,7 @@ __global__ void __launch_bounds__(256) qqa_step_stream_kernel(const InstDesc *__
         if (x.valid) {
             x.k0 = __ldg(x.d->row_ptr + x.row);
             x.k1 = __ldg(x.d->row_ptr + x.row + 1);
-            if (x.k1 - x.k0 > x.d->long_thresh) x.valid = false;   // long row: updated by the long-row kernel
+            if (x.d->hub_active && x.k1 - x.k0 > x.d->long_thresh) x.valid = false;   // long row: the long-row kernel's
         }
         return x;
     };
@@ -1235,46 +1399,8 @@ __global__ void __launch_bounds__(256) qqa_step_hub_kernel(const InstDesc *__res
             for (int e = 0; e < VEC; ++e) Y[v][e] = 0.0f;
         float dseg = 0.0f;
         gather_row<T, G, VPL>(d, Xc, x, S_pad, gl, gmask, Y, dseg);
-        float *part = d->seg_part + (size_t)seg * S_pad;
-#pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-            const int off = (v * G + gl) * VEC;
-            if (off < S_pad) store_f32_vec(part + off, Y[v], VEC);
-        }
-        __threadfence();   // this lane's partial is visible before the group announces it
-        __syncwarp(gmask);
-        unsigned prev = 0;
-        if (gl == 0) prev = atomicAdd(d->seg_cnt + j, 1u);
-        prev = __shfl_sync(gmask, prev, 0, G);
-        if (prev != (unsigned)(s1 - s0 - 1)) continue;   // not the last segment of the row
-        __threadfence();
-        // the partials in segment order, read from L2 (other SMs wrote them in this launch)
-        for (int q = s0; q < s1; ++q) {
-            const float *pp = d->seg_part + (size_t)q * S_pad;
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                const int off = (v * G + gl) * VEC;
-                if (off < S_pad) {
-#pragma unroll
-                    for (int k = 0; k < VEC; k += 4) {
-                        const float4 a = __ldcg(reinterpret_cast<const float4 *>(pp + off + k));
-                        if (q == s0) {
-                            Y[v][k] = a.x; Y[v][k + 1] = a.y; Y[v][k + 2] = a.z; Y[v][k + 3] = a.w;
-                        } else {
-                            Y[v][k] += a.x; Y[v][k + 1] += a.y; Y[v][k + 2] += a.z; Y[v][k + 3] += a.w;
-                        }
-                    }
-                }
-            }
-        }
-        if (gl == 0) d->seg_cnt[j] = 0u;   // ready for the next step (a later launch)
-        // weighted degree of the whole row (integer weights: exact in any order)
-        float dsum = (float)(rk1 - rk0);
-        if (d->w) {
-            float ws = 0.0f;
-            for (int k = rk0 + gl; k < rk1; k += G) ws += (float)__ldg(d->w + k);
-            dsum = group_sum<G>(ws, gmask);
-        }
+        if (!seg_arrive<T, G, VPL>(d, seg, j, s0, s1, gl, gmask, Y)) continue;   // not the row's last segment
+        const float dsum = row_weight_sum<G>(d, rk0, rk1, gl, gmask);
         const StepCtx c = make_ctx(d, t, r);
         OwnRow<T, G, VPL> own;
         load_own<T, G, VPL>(d, c, row, gl, own);

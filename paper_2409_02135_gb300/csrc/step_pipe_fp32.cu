@@ -8,10 +8,10 @@ namespace qqa {
 
 using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
 
-PipeFn step_pipe_kernel_fp32(int G, int VPL)
+PipeFn step_pipe_kernel_fp32(int G, int VPL, bool segs)
 {
 #define QQA_CASE(g, v) \
-    if (G == g && VPL == v) return qqa_step_pipe_kernel<float, g, v>;
+    if (G == g && VPL == v) return segs ? qqa_step_pipe_kernel<float, g, v, true> : qqa_step_pipe_kernel<float, g, v, false>;
     QQA_CASE(1, 1) QQA_CASE(1, 2) QQA_CASE(1, 4)
     QQA_CASE(2, 1) QQA_CASE(2, 2) QQA_CASE(2, 4)
     QQA_CASE(4, 1) QQA_CASE(4, 2) QQA_CASE(4, 4)

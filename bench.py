@@ -241,17 +241,44 @@ def sum_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------ time to quality
+# oracle result sets (tests/golden/oracle_quality_<set>.json) per workload, the
+# one with more runs per instance first
+GOLDEN_SETS = {"mis_er700_800": ["mis_er700_800_s16", "mis_er700_800"], "mis_er100": ["mis_er100"],
+               "maxcut_regular3": ["maxcut_regular3_n100000"], "maxcut_ba4": ["maxcut_ba4_n100000"]}
+
+
+def oracle_targets(workload: str):
+    """Per instance (in workload order): the oracle's mean final best objective
+    and the number of oracle runs it is the mean of; None where no set has it."""
+    out = None
+    for name in GOLDEN_SETS.get(workload, []):
+        path = os.path.join(ROOT, "tests", "golden", f"oracle_quality_{name}.json")
+        if not os.path.exists(path):
+            continue
+        recs = json.load(open(path))["instances"]
+        if out is None:
+            out = [None] * 0
+        for j, rec in enumerate(recs):
+            while len(out) <= j:
+                out.append(None)
+            if out[j] is None and rec.get("oracle_mean_best") is not None:
+                out[j] = (float(rec["oracle_mean_best"]), len(rec["oracle_best"]))
+    return out
+
+
 def time_to_quality(workload: str, run, count: int, anneal_start, chunk_events, R: int):
     """Seconds from the start of the last timed anneal until each instance's
     best feasible objective (periodic rounding after every chunk) first reaches
     99% of the oracle's mean final best (tests/golden/oracle_quality_*.json)."""
-    path = os.path.join(ROOT, "tests", "golden", f"oracle_quality_{workload}.json")
-    if not os.path.exists(path):
+    ref = oracle_targets(workload)
+    if not ref:
         return None
-    ref = json.load(open(path))["instances"]
     times, reached = [], 0
+    runs_per_target = sorted({r[1] for r in ref[:count] if r})
     for j in range(min(count, len(ref))):
-        target = ref[j]["oracle_mean_best"]
+        if ref[j] is None:
+            continue
+        target = ref[j][0]
         hist, at = run.history(j)
         t_hit = None
         for e, (best, step) in enumerate(zip(hist, at)):
@@ -261,11 +288,12 @@ def time_to_quality(workload: str, run, count: int, anneal_start, chunk_events, 
         if t_hit is not None:
             reached += 1
             times.append(t_hit)
+    target = f"0.99 x oracle mean final best ({'/'.join(map(str, runs_per_target))} oracle runs per instance)"
     if not times:
-        return {"reached": 0, "instances": min(count, len(ref))}
+        return {"reached": 0, "instances": min(count, len(ref)), "target": target}
     times.sort()
     return {"median_s": times[len(times) // 2], "max_s": times[-1], "reached": reached,
-            "instances": min(count, len(ref)), "target": "0.99 x oracle mean final best (4 seeds)"}
+            "instances": min(count, len(ref)), "target": target}
 
 
 def time_to_quality_plain(workload: str, runs1, job_start, chunk_end_events):
@@ -273,13 +301,14 @@ def time_to_quality_plain(workload: str, runs1, job_start, chunk_end_events):
     start of the job until instance j's best feasible objective first reaches
     99% of the oracle's mean final best (its wait for the earlier instances
     included)."""
-    path = os.path.join(ROOT, "tests", "golden", f"oracle_quality_{workload}.json")
-    if not os.path.exists(path):
+    ref = oracle_targets(workload)
+    if not ref:
         return None
-    ref = json.load(open(path))["instances"]
     times = []
     for j in range(min(len(runs1), len(ref))):
-        target = ref[j]["oracle_mean_best"]
+        if ref[j] is None:
+            continue
+        target = ref[j][0]
         hist, _ = runs1[j].history(0)
         for e, best in enumerate(hist):
             if best > -(2 ** 62) and best >= 0.99 * target and e < len(chunk_end_events[j]):
@@ -290,7 +319,7 @@ def time_to_quality_plain(workload: str, runs1, job_start, chunk_end_events):
     reached = len(times)
     times.sort()
     return {"median_s": times[len(times) // 2], "max_s": times[-1], "reached": reached,
-            "instances": min(len(runs1), len(ref)), "target": "0.99 x oracle mean final best (4 seeds)"}
+            "instances": min(len(runs1), len(ref)), "target": "0.99 x oracle mean final best"}
 
 
 # ----------------------------------------------------------------- oracle leg
@@ -341,6 +370,79 @@ def run_reference(args):
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------ sub-records
+def workload_record(name: str, local: int, stream, alloc, flush, timed: int = 3, warmup: int = 2):
+    """One more workload measured the way the headline is (device-timed whole
+    anneals after an autotuned launch shape, L2 flushed between anneals,
+    clocks sampled while timing): replica-steps/s, the step kernel's roofline,
+    the best objective and the time to the oracle's quality. Used for the
+    graded HBM-bound max-cut configurations beside the default workload."""
+    import torch
+    import paper_2409_02135_gb300 as qqa
+    wl = build_workload(name, 0)
+    probs = [qqa.Problem(inst.kind, inst.graph, stream=stream, allocator=alloc) for inst in wl.instances]
+    params = [qqa.make_params(inst.params) for inst in wl.instances]
+    cfg, tuned_us = qqa.autotune(probs, params, trial_steps=100, stream=stream, allocator=alloc)
+    cfg.use_graphs = 1
+    run = qqa.Run.create(probs, params, config=cfg, stream=stream, allocator=alloc)
+    K = max(p.steps for p in params)
+    R = min(p.round_every for p in params) or K
+    chunks = (K + R - 1) // R
+    replica_steps = sum(p.S * p.steps for p in params)
+
+    def anneal(seed, ev=None):
+        run.reset(seed)
+        for c in range(chunks):
+            if ev is not None:
+                ev[c][0].record(stream)
+            run.steps(min(R, K - c * R))
+            if ev is not None:
+                ev[c][1].record(stream)
+            run.eval()
+
+    for w in range(warmup):
+        anneal(11_000 + w)
+    torch.cuda.synchronize()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(chunks)]
+          for _ in range(timed)]
+    se = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(timed)]
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        for k in range(timed):
+            flush.zero_()
+            se[k][0].record(stream)
+            anneal(21_000 + k, ev[k])
+            se[k][1].record(stream)
+        torch.cuda.synchronize()
+    run.sync()
+    ms = [a.elapsed_time(b) for a, b in se]
+    step_ms = sum(a.elapsed_time(b) for e in ev for a, b in e)
+    avg_launch_s = step_ms / 1000.0 / (timed * K)
+    alg = algorithmic_bytes_per_launch(wl)
+    peak, peak_kind = read_peak()
+    variant = KERNEL_NAMES[run.config().kernel]
+    res = run.result(0, with_x=False)
+    c = run.config()
+    rec = {"workload": wl.name, "value": replica_steps / (statistics.mean(ms) / 1000.0), "unit": METRIC,
+           "ms_per_anneal": statistics.mean(ms), "anneals": timed, "warmup": warmup,
+           "dtype": "f32" if wl.instances[0].params.precision == W.FP32 else "bf16-storage/f32-math",
+           "launch": {"kernel": variant, "group_lanes": c.group_lanes, "vec_per_lane": c.vec_per_lane,
+                      "block_threads": c.block_threads, "grid_blocks": c.grid_blocks, "autotuned": True},
+           "roofline": {"bound": "hbm", "achieved": alg / avg_launch_s / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / avg_launch_s / 1e9 / peak, "traffic": profiled_traffic(name, variant),
+                        "peak_source": peak_kind, "kernel": KERNEL_SYMBOL[variant],
+                        "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_launch_s * 1e6,
+                        "step_share_of_device_time": step_ms / sum(ms)},
+           "clocks": clocks.summary(),
+           "best_objective": int(res["obj"][res["best"]]) if res["best"] >= 0 else None,
+           "time_to_oracle_quality": time_to_quality(name, run, len(probs), se[-1][0], ev[-1], R),
+           "l2": "flushed between timed anneals (512 MB write)"}
+    run.close()
+    for pb in probs:
+        pb.close()
+    return rec
 
 
 # -------------------------------------------------------------------- our leg
@@ -443,24 +545,34 @@ def run_ours(args):
                   for i in wl.instances)
         d2h = sum(p.S * (8 + 8 + 1 + 8) + 4 + 4 * ((i.graph.n + 31) // 32) for p, i in zip(params, wl.instances))
         times = []
+        phases = {"problems_s": [], "anneal_s": [], "results_s": [], "release_s": []}
         for k in range(args.e2e_steps + 1):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             eprobs = [qqa.Problem(i.kind, i.graph, stream=stream, allocator=alloc) for i in wl.instances]
             eparams = [qqa.make_params(i.params, seed=30_000 + k) for i in wl.instances]
+            t1 = time.perf_counter()
             erun = qqa.anneal(eprobs, eparams, config=cfg, stream=stream, allocator=alloc)
+            t2 = time.perf_counter()
             out = [erun.result(j) for j in range(len(eprobs))]
+            t3 = time.perf_counter()
             erun.close()
             for pb in eprobs:
                 pb.close()
             dt = time.perf_counter() - t0
             if k > 0:                     # the first call also builds the CUDA graphs
                 times.append(dt)
+                for key, v in zip(phases, (t1 - t0, t2 - t1, t3 - t2, t0 + dt - t3)):
+                    phases[key].append(v)
             assert all(o["best"] >= -1 for o in out)
         e2e_s = max_over_ranks(sum(times), world)
         e2e = {"value": sum_over_ranks(replica_steps * len(times), world) / e2e_s, "unit": METRIC,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(times)}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": len(times),
+               "host_phases_ms": {key: 1000 * statistics.mean(v) for key, v in phases.items()},
+               "device_anneal_ms": statistics.mean(ms),
+               "phases": "problems = CSR checks and uploads; anneal = run set-up, all steps and roundings, "
+                         "synchronisation; results = per-instance copies; release = frees"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -569,6 +681,10 @@ def run_ours(args):
                                            for q, i in zip(quality, wl.instances)],
         "time_to_oracle_quality": ttq, "plain": plain, "batched_bf16": bf16,
     }
+    # the graded HBM-bound configurations (max-cut n = 1e5, S = 256, BF16) beside the default workload
+    if args.workload == "mis_er700_800" and world == 1 and not args.no_subrecords:
+        for name in ("maxcut_regular3", "maxcut_ba4"):
+            line[name] = workload_record(name, local, stream, alloc, flush)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -788,10 +904,12 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the launch-shape autotuner (runs before the timed region)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-instance-at-a-time comparison")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the max-cut n = 1e5 records added to the default workload's line")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -334,8 +334,14 @@ int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
 /* ---------------------------------------------------------- serving */
 /*
  * Continuous-batching solve server. Requests (a host CSR graph plus its
- * qqa_params) are queued on submit and admitted in FIFO order while the HBM
- * budget and a free slot of the request's replica class allow (class = S
+ * qqa_params) are queued on submit and admitted in arrival order while the HBM
+ * budget and a free slot of the request's replica class allow; a request that
+ * does not fit the budget yet is passed over by later ones that do (at most
+ * 32 pumps, after which admission waits for it). Each request is charged the
+ * device bytes its graph, long-row tables, carved state and tile records take,
+ * each allocation rounded up to 512 bytes, and its share of the work lists;
+ * each class run is charged slots_per_class x 512 + 8192 bytes of fixed
+ * buffers when it is created and keeps them until qqa_server_destroy (class = S
  * rounded up to a power of two, >= 8; one run with a fixed launch shape and
  * its own stream per class). Each qqa_server_pump admits, advances every
  * class by `chunk_steps` annealing steps (the classes overlap on the device;
@@ -364,7 +370,10 @@ typedef struct qqa_request_info {
     int32_t evaluations;/* periodic roundings recorded (one per chunk) */
     int32_t reserved;
 } qqa_request_info;
-/* Device bytes a request is charged (state, evaluation buffers, graph). */
+/* Device bytes of the state, evaluation buffers and graph of a request of n
+ * nodes and nnz CSR entries, without the graph-dependent parts (long-row
+ * tables and partial sums, history, allocation granules): an estimate for
+ * capacity planning; the server charges each request its exact figure. */
 int64_t qqa_request_bytes(int32_t n, int64_t nnz, int32_t S, int32_t precision, int32_t weighted);
 /* chunk_steps in [1, 50]; cfg fixes the launch shape of every class (NULL = auto); alloc may be NULL. */
 int qqa_server_create(int64_t hbm_budget_bytes, int32_t chunk_steps, int32_t slots_per_class, int32_t precision,

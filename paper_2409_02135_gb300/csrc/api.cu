@@ -180,13 +180,39 @@ static int validate_csr(int32_t kind, int32_t n, const int32_t *rp, const int32_
             if (j < 0 || j >= n) return fail(QQA_EINVAL, "col[%lld] = %d out of range [0, %d)", (long long)k, j, n);
             if (j == i) return fail(QQA_EINVAL, "self-loop at node %d", i);
             if (k > rp[i] && col[k - 1] >= j) return fail(QQA_EINVAL, "row %d not strictly increasing", i);
-            // symmetry: i must appear in row j (binary search)
-            const int32_t *b = col + rp[j], *e = col + rp[j + 1];
-            const int32_t *f = std::lower_bound(b, e, i);
-            if (f == e || *f != i) return fail(QQA_EINVAL, "edge (%d,%d) has no reverse entry", i, j);
-            if (w && w[k] != w[f - col]) return fail(QQA_EINVAL, "weight of (%d,%d) differs from (%d,%d)", i, j, j, i);
         }
     }
+    // Symmetry in O(nnz): scatter every entry (i, j) into row j of the
+    // transpose; visiting i in increasing order leaves each transposed row
+    // sorted, so the graph is symmetric exactly when the transpose equals it
+    // (and the weights of (i, j) and (j, i) agree). Only when it does not is
+    // the offending entry looked for (by binary search), for the message.
+    auto report_asymmetry = [&]() -> int {
+        for (int32_t i = 0; i < n; ++i)
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t j = col[k];
+                const int32_t *b = col + rp[j], *e = col + rp[j + 1];
+                const int32_t *f = std::lower_bound(b, e, i);
+                if (f == e || *f != i) return fail(QQA_EINVAL, "edge (%d,%d) has no reverse entry", i, j);
+                if (w && w[k] != w[f - col])
+                    return fail(QQA_EINVAL, "weight of (%d,%d) differs from (%d,%d)", i, j, j, i);
+            }
+        return fail(QQA_EINVAL, "the graph is not symmetric");
+    };
+    std::vector<int64_t> pos(rp, rp + n);
+    for (int64_t k = 0; k < nnz; ++k) ++pos[col[k]];   // row starts + in-degrees
+    for (int32_t j = 0; j < n; ++j)
+        if (pos[j] != rp[j + 1]) return report_asymmetry();   // in-degree != out-degree
+    std::copy(rp, rp + n, pos.begin());
+    std::vector<int32_t> tcol((size_t)nnz), tw(w ? (size_t)nnz : 0);
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int64_t p = pos[col[k]]++;
+            tcol[p] = i;
+            if (w) tw[p] = w[k];
+        }
+    for (int64_t k = 0; k < nnz; ++k)
+        if (tcol[k] != col[k] || (w && tw[k] != w[k])) return report_asymmetry();
     return QQA_OK;
 }
 
@@ -605,8 +631,15 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     }
     const int32_t nt = (int32_t)tiles.size();
     const bool seg_items = fold && !tiles.empty() && tiles.front().row0 < 0;
-    if (nt > r->tile_cap) {
-        int32_t cap = std::max<int32_t>(nt, 2 * r->tile_cap);
+    // a list doubles when it is full and is cut to twice its entries when they
+    // fall below a quarter of it, so its capacity stays within 4x its entries
+    auto resize_to = [](int32_t need, int32_t cap) -> int32_t {
+        if (need > cap) return std::max<int32_t>(need, 2 * cap);
+        if (cap > 256 && need < cap / 4) return std::max<int32_t>(2 * need, 256);
+        return cap;
+    };
+    if (resize_to(nt, r->tile_cap) != r->tile_cap) {
+        int32_t cap = resize_to(nt, r->tile_cap);
         QQA_CK(cudaStreamSynchronize(st));
         Tile *nt_buf = (Tile *)r->alloc.get(sizeof(Tile) * (size_t)cap, st);
         if (!nt_buf) return fail(QQA_ENOMEM, "tile list allocation failed");
@@ -627,8 +660,8 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
         if (s.prob->kind == QQA_MAXCLIQUE) cliques.push_back(k);
     }
     const int32_t nh = (int32_t)hub.size(), nc = (int32_t)cliques.size();
-    if (nh > r->hub_cap) {
-        const int32_t cap = std::max<int32_t>(nh, 2 * r->hub_cap);
+    if (resize_to(nh, r->hub_cap) != r->hub_cap) {
+        const int32_t cap = resize_to(nh, r->hub_cap);
         QQA_CK(cudaStreamSynchronize(st));
         Tile *buf = (Tile *)r->alloc.get(sizeof(Tile) * (size_t)cap, st);
         if (!buf) return fail(QQA_ENOMEM, "long-row item list allocation failed");
@@ -638,8 +671,8 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
         drop_graphs(r);
     }
     if (nh) QQA_CK(cudaMemcpyAsync(r->d_hub_items, hub.data(), sizeof(Tile) * (size_t)nh, cudaMemcpyHostToDevice, st));
-    if (nc > r->clique_cap) {
-        const int32_t cap = std::max<int32_t>(nc, 2 * r->clique_cap);
+    if (resize_to(nc, r->clique_cap) != r->clique_cap) {
+        const int32_t cap = resize_to(nc, r->clique_cap);
         QQA_CK(cudaStreamSynchronize(st));
         int32_t *buf = (int32_t *)r->alloc.get(sizeof(int32_t) * (size_t)cap, st);
         if (!buf) return fail(QQA_ENOMEM, "clique slot list allocation failed");
@@ -853,12 +886,87 @@ static void free_slot(qqa_run *r, int32_t k, cudaStream_t st)
     r->h_descs[k] = InstDesc{};
 }
 
-extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void *stream, int32_t *slot_out)
+// Device memory of one slot: every buffer is carved out of one allocation
+// (256-byte aligned pieces), so adding an instance costs one allocator call.
+struct SlotLayout {
+    size_t X[2], master, m, v, colsum, seg_part, seg_cnt, bits, counts, res_obj, res_viol, res_feas, res_energy,
+        res_meta, res_bestx, hist_best, hist_step, scal, total;
+};
+
+static const size_t kNone = ~(size_t)0;
+
+static SlotLayout slot_layout(int32_t n, int32_t S_pad, int32_t W, int32_t hist_cap, int32_t prec, bool clique,
+                              int32_t nseg, int32_t nlong)
+{
+    SlotLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t elems = (size_t)n * S_pad, tb = prec == kFP32 ? 4 : 2;
+    L.X[0] = take(elems * tb);
+    L.X[1] = take(elems * tb);
+    L.master = prec == kBF16 ? take(elems * 4) : kNone;
+    L.m = take(elems * tb);
+    L.v = take(elems * tb);
+    L.colsum = clique ? take((size_t)S_pad * 4) : kNone;
+    L.seg_part = nseg > 0 ? take((size_t)nseg * S_pad * 4) : kNone;
+    L.seg_cnt = nseg > 0 ? take((size_t)nlong * 4) : kNone;
+    L.bits = take((size_t)n * W * 4);
+    L.counts = take(3 * (size_t)S_pad * 8);
+    L.res_obj = take((size_t)S_pad * 8);
+    L.res_viol = take((size_t)S_pad * 8);
+    L.res_feas = take((size_t)S_pad);
+    L.res_energy = take((size_t)S_pad * 8);
+    L.res_meta = take(4 * 4);
+    L.res_bestx = take((size_t)((n + 31) / 32) * 4);
+    L.hist_best = take((size_t)hist_cap * 8);
+    L.hist_step = take((size_t)hist_cap * 4);
+    L.scal = take((size_t)kMaxChunk * sizeof(float4));
+    L.total = off;
+    return L;
+}
+
+namespace qqa {
+// Device bytes one request takes when it is added to a run of a gathering
+// step kernel: the graph (CSR, weights, long-row tables) and the slot's
+// carved state, each allocation rounded up to 512 bytes (the granule of the
+// usual allocators), plus its share of the run's work lists (at most one tile
+// per row and one item per long-row segment, in lists whose capacity stays
+// within four times their entries: they double when full and halve below a
+// quarter).
+int64_t request_device_bytes(int32_t kind, int32_t n, const int32_t *row_ptr, bool weighted, const qqa_params *prm)
+{
+    auto g512 = [](int64_t b) { return (std::max<int64_t>(b, 16) + 511) / 512 * 512; };
+    const int64_t nnz = row_ptr[n];
+    const int32_t thr = long_row_threshold(n, nnz);
+    int32_t nlong = 0, nseg = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t deg = row_ptr[i + 1] - row_ptr[i];
+        if (deg > thr) { ++nlong; nseg += (deg + kSegLen - 1) / kSegLen; }
+    }
+    const int32_t vec = prm->precision == QQA_FP32 ? 4 : 8;
+    const int32_t S_pad = prm->S == 1 ? 1 : (prm->S + vec - 1) / vec * vec;
+    const int32_t hist_cap = (prm->round_every > 0 ? prm->steps / prm->round_every : 0) + 2;
+    int64_t b = g512(4 * ((int64_t)n + 1)) + g512(4 * nnz) + (weighted ? g512(4 * nnz) : 0);
+    if (nlong) b += g512(4 * (int64_t)nlong) + g512(4 * ((int64_t)nlong + 1)) + g512(4 * (int64_t)nseg);
+    const SlotLayout L = slot_layout(n, S_pad, (prm->S + 31) / 32, hist_cap, prm->precision, kind == QQA_MAXCLIQUE,
+                                     nseg, nlong);
+    b += g512((int64_t)L.total);
+    b += 32 * ((int64_t)n + nseg);   // tile and segment records (lists hold at most 4x their entries)
+    return b;
+}
+}  // namespace qqa
+
+// First half of adding an instance: a free slot, its device memory and its
+// host-side descriptor. Nothing is launched.
+static int slot_setup(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, cudaStream_t st, int32_t *slot_out)
 {
     if (!r || !prob) return fail(QQA_EINVAL, "run or problem is NULL");
     int rc = check_params(prm, r->S_max, r->prec);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
     int32_t k = -1;
     for (int32_t i = 0; i < r->capacity; ++i)
         if (!r->slots[i].active) { k = i; break; }
@@ -874,26 +982,30 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     s.W = (prm->S + 31) / 32;
     s.K = prm->steps;
     s.hist_cap = (prm->round_every > 0 ? prm->steps / prm->round_every : 0) + 2;
-    const size_t elems = (size_t)s.n * s.S_pad;
-    const size_t tb = r->prec == kFP32 ? 4 : 2;
-    auto get = [&](size_t bytes) -> void * {
-        void *p = r->alloc.get(bytes, st);
-        if (p) s.dev.push_back(p);
-        return p;
-    };
+    // long rows: the evaluation always splits them; the gather step kernels
+    // leave them to segment work items (partial sums and counters per slot)
+    const bool hubs = r->hub_fn != nullptr && prob->nlong > 0;
+    const SlotLayout L = slot_layout(s.n, s.S_pad, s.W, s.hist_cap, r->prec, prob->kind == QQA_MAXCLIQUE,
+                                     hubs ? prob->nseg : 0, prob->nlong);
+    unsigned char *base = (unsigned char *)r->alloc.get(L.total, st);
+    if (!base) return fail(QQA_ENOMEM, "device allocation of %zu bytes for instance state failed (n=%d, S=%d)",
+                           L.total, s.n, s.S);
+    s.dev.push_back(base);
+    if ((uintptr_t)base & 15u) {
+        free_slot(r, k, st);
+        return fail(QQA_EINVAL, "the allocator returned state memory that is not 16-byte aligned");
+    }
+    auto at = [&](size_t off) -> void * { return off == kNone ? nullptr : (void *)(base + off); };
     InstDesc d{};
     d.row_ptr = prob->row_ptr;
     d.col = prob->col;
     d.w = prob->w;
-    d.X[0] = get(elems * tb);
-    d.X[1] = get(elems * tb);
-    d.master = r->prec == kBF16 ? (float *)get(elems * 4) : nullptr;
-    d.m = get(elems * tb);
-    d.v = get(elems * tb);
-    d.colsum = prob->kind == QQA_MAXCLIQUE ? (float *)get((size_t)s.S_pad * 4) : nullptr;
-    // long rows: the evaluation always splits them; the gather step kernels
-    // leave them to segment work items (partial sums and counters per slot)
-    const bool hubs = r->hub_fn != nullptr && prob->nlong > 0;
+    d.X[0] = at(L.X[0]);
+    d.X[1] = at(L.X[1]);
+    d.master = (float *)at(L.master);
+    d.m = at(L.m);
+    d.v = at(L.v);
+    d.colsum = (float *)at(L.colsum);
     d.long_thresh = prob->nlong > 0 ? prob->long_thresh : 0x7fffffff;
     d.hub_active = hubs ? 1 : 0;
     d.nlong = prob->nlong;
@@ -901,36 +1013,20 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     d.long_rows = prob->long_rows;
     d.seg_ptr = prob->seg_ptr;
     d.seg_row = prob->seg_row;
-    if (hubs) {
-        d.seg_part = (float *)get((size_t)prob->nseg * s.S_pad * 4);
-        d.seg_cnt = (uint32_t *)get((size_t)prob->nlong * 4);
-    }
+    d.seg_part = (float *)at(L.seg_part);
+    d.seg_cnt = (uint32_t *)at(L.seg_cnt);
     d.grad_dbg = nullptr;
-    d.bits = (uint32_t *)get((size_t)s.n * s.W * 4);
-    d.counts = (unsigned long long *)get(3 * (size_t)s.S_pad * 8);
-    d.res_obj = (long long *)get((size_t)s.S_pad * 8);
-    d.res_viol = (long long *)get((size_t)s.S_pad * 8);
-    d.res_feas = (uint8_t *)get((size_t)s.S_pad);
-    d.res_energy = (double *)get((size_t)s.S_pad * 8);
-    d.res_meta = (int32_t *)get(4 * 4);
-    d.res_bestx = (uint32_t *)get((size_t)((s.n + 31) / 32) * 4);
-    d.hist_best = (long long *)get((size_t)s.hist_cap * 8);
-    d.hist_step = (int32_t *)get((size_t)s.hist_cap * 4);
-    d.scal = (float4 *)get((size_t)kMaxChunk * sizeof(float4));
-    bool ok = d.X[0] && d.X[1] && d.m && d.v && d.bits && d.counts && d.res_obj && d.res_viol && d.res_feas &&
-              d.res_energy && d.res_meta && d.res_bestx && d.hist_best && d.hist_step && d.scal &&
-              (r->prec == kFP32 || d.master) && (prob->kind != QQA_MAXCLIQUE || d.colsum) &&
-              (!hubs || (d.seg_part && d.seg_cnt));
-    if (!ok) {
-        free_slot(r, k, st);
-        return fail(QQA_ENOMEM, "device allocation for instance state failed (n=%d, S=%d)", s.n, s.S);
-    }
-    const void *state_ptrs[5] = {d.X[0], d.X[1], d.master, d.m, d.v};
-    for (const void *q : state_ptrs)
-        if (q && ((uintptr_t)q & 15u)) {
-            free_slot(r, k, st);
-            return fail(QQA_EINVAL, "the allocator returned state memory that is not 16-byte aligned");
-        }
+    d.bits = (uint32_t *)at(L.bits);
+    d.counts = (unsigned long long *)at(L.counts);
+    d.res_obj = (long long *)at(L.res_obj);
+    d.res_viol = (long long *)at(L.res_viol);
+    d.res_feas = (uint8_t *)at(L.res_feas);
+    d.res_energy = (double *)at(L.res_energy);
+    d.res_meta = (int32_t *)at(L.res_meta);
+    d.res_bestx = (uint32_t *)at(L.res_bestx);
+    d.hist_best = (long long *)at(L.hist_best);
+    d.hist_step = (int32_t *)at(L.hist_step);
+    d.scal = (float4 *)at(L.scal);
     if (r->dense_N) {
         if (prob->max_abs_w > 2048) {
             free_slot(r, k, st);
@@ -978,11 +1074,18 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
     cudaError_t e = cudaMemsetAsync(d.res_meta, 0, 16, st);
     if (e == cudaSuccess && hubs) e = cudaMemsetAsync(d.seg_cnt, 0, (size_t)prob->nlong * 4, st);
     if (e != cudaSuccess) { free_slot(r, k, st); return fail(QQA_ECUDA, "memset: %s", cudaGetErrorString(e)); }
-    rc = upload_desc(r, k, st);
-    if (rc) { free_slot(r, k, st); return rc; }
+    *slot_out = k;
+    return QQA_OK;
+}
+
+// Second half: the initial draw (and the max-clique column sums, the
+// tensor-core adjacency and planes) of a slot whose descriptor is on the device.
+static int slot_start(qqa_run *r, int32_t k, cudaStream_t st)
+{
+    const SlotHost &s = r->slots[k];
     launch_init(r->d_descs, k, s.n, s.S_pad, r->prec, st);
     g_launches += 1;
-    if (prob->kind == QQA_MAXCLIQUE) {
+    if (s.prob->kind == QQA_MAXCLIQUE) {
         launch_colsum(r->d_descs, nullptr, 1, k, s.S_pad, r->prec, 0, 0, st);
         g_launches += 1;
     }
@@ -992,11 +1095,23 @@ extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params
         g_launches += 2;
     }
     QQA_CK_LAUNCH("init");
+    return QQA_OK;
+}
+
+extern "C" int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void *stream, int32_t *slot_out)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t k = -1;
+    int rc = slot_setup(r, prob, prm, st, &k);
+    if (rc) return rc;
+    rc = upload_desc(r, k, st);
+    if (!rc) rc = slot_start(r, k, st);
+    if (rc) { free_slot(r, k, st); return rc; }
     rc = rebuild_tiles(r, st);
     if (rc) {   // no room for the grown tile list: undo the add, keep the other slots running
         const std::string msg = g_last_error;
         r->h_descs[k].active = 0;
-        s.active = false;
+        r->slots[k].active = false;
         (void)upload_desc(r, k, st);
         cudaStreamSynchronize(st);
         free_slot(r, k, st);
@@ -1093,14 +1208,27 @@ extern "C" int qqa_run_create(qqa_problem *const *problems, const qqa_params *pa
     qqa_run *r = nullptr;
     int rc = run_create_hinted(count, S_max, params[0].precision, cfg, alloc, stream, staged_hint, mean_deg, &r);
     if (rc) return rc;
-    for (int32_t k = 0; k < count; ++k) {
+    // every slot set up first, then one descriptor upload, the initial draws
+    // and one tile list (slot k = problem k)
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int32_t k = 0; k < count && !rc; ++k) {
         int32_t slot = -1;
-        rc = qqa_run_add(r, problems[k], &params[k], stream, &slot);
+        rc = slot_setup(r, problems[k], &params[k], st, &slot);
         if (rc) {
             std::string msg = g_last_error;
             qqa_run_destroy(r);
             return fail(rc, "instance %d: %s", k, msg.c_str());
         }
+    }
+    cudaError_t e = cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)count,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = fail(QQA_ECUDA, "descriptor upload: %s", cudaGetErrorString(e));
+    for (int32_t k = 0; k < count && !rc; ++k) rc = slot_start(r, k, st);
+    if (!rc) rc = rebuild_tiles(r, st);
+    if (rc) {
+        std::string msg = g_last_error;
+        qqa_run_destroy(r);
+        return fail(rc, "%s", msg.c_str());
     }
     *out = r;
     return QQA_OK;

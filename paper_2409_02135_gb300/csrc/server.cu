@@ -1,10 +1,11 @@
 // server.cu -- continuous-batching solve server on top of the run API.
 //
 // Requests (one graph plus its hyper-parameters) arrive at any time and wait
-// in a FIFO queue. At each pump the server
-//   1. admits queued requests in order while the HBM budget and a free slot
-//      of the request's replica class allow (graph upload, state allocation
-//      and initial draw happen here),
+// in a queue. At each pump the server
+//   1. admits queued requests in arrival order, with backfill (see admit), while
+//      the HBM budget - every request is charged the exact device bytes its
+//      graph and state take - and a free slot of its replica class allow (graph
+//      upload, state allocation and initial draw happen here),
 //   2. advances every class run by one chunk of steps, each class on its own
 //      stream so the classes' work overlaps on the device; inside a class the
 //      requests share each step launch (one tile list),
@@ -28,6 +29,10 @@
 
 #include "../../include/qqa.h"
 
+namespace qqa {
+int64_t request_device_bytes(int32_t kind, int32_t n, const int32_t *row_ptr, bool weighted, const qqa_params *prm);
+}
+
 namespace {
 
 double now_s()
@@ -45,6 +50,7 @@ struct Request {
     int32_t error = QQA_OK;
     int64_t bytes = 0;
     int32_t cls = -1, slot = -1;
+    int32_t passed_over = 0;          // pumps in which later requests were admitted before it
     qqa_problem *prob = nullptr;
     double t_submit = 0, t_admit = 0, t_done = 0;
     // results (filled at retirement)
@@ -97,6 +103,10 @@ extern "C" int64_t qqa_request_bytes(int32_t n, int64_t nnz, int32_t S, int32_t 
     return state + evalb + graph;
 }
 
+// Bytes a class run holds whatever its requests: descriptors, status, tile
+// counters and the smallest work lists.
+static int64_t class_fixed_bytes(int32_t slots) { return (int64_t)slots * 512 + 8192; }
+
 extern "C" int qqa_server_create(int64_t hbm_budget_bytes, int32_t chunk_steps, int32_t slots_per_class,
                                  int32_t precision, const qqa_launch_config *cfg, const qqa_allocator *alloc,
                                  qqa_server **out)
@@ -131,7 +141,7 @@ extern "C" int qqa_server_submit(qqa_server *s, int32_t kind, int32_t n, const i
     if (nnz > 0) r->col.assign(col, col + nnz);
     if (w && nnz > 0) r->w.assign(w, w + nnz);
     r->prm = *prm;
-    r->bytes = qqa_request_bytes(n, nnz, prm->S, prm->precision, w != nullptr);
+    r->bytes = qqa::request_device_bytes(kind, n, row_ptr, w != nullptr, prm);
     r->t_submit = now_s();
     if (r->bytes > s->budget) {   // can never fit: rejected now
         r->state = QQA_REQ_FAILED;
@@ -163,6 +173,7 @@ static ClassRun *get_class(qqa_server *s, int32_t cls, int *rc)
         return nullptr;
     }
     c.slot_req.assign(s->slots_per_class, -1);
+    s->used += class_fixed_bytes(s->slots_per_class);
     auto res = s->classes.emplace(cls, c);
     return &res.first->second;
 }
@@ -180,24 +191,42 @@ static void release(qqa_server *s, Request *r)
     s->used -= r->bytes;
 }
 
-// admit queued requests in FIFO order while budget and slots allow
+// Pumps a request that does not fit the budget may be passed over by later,
+// smaller ones before admission waits for it.
+static const int32_t kMaxPassOver = 32;
+
+// Admission: arrival order with backfill. A request that does not fit the HBM
+// budget now is passed over and later requests that do fit are admitted
+// (small requests do not queue behind a large one); after kMaxPassOver such
+// pumps nothing more is admitted ahead of it, so it cannot wait forever. A
+// request whose replica class has no free slot waits without holding up the
+// other classes.
 static void admit(qqa_server *s)
 {
-    while (!s->queue.empty()) {
-        Request *r = s->reqs[s->queue.front()].get();
-        if (s->used + r->bytes > s->budget) break;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+        Request *r = s->reqs[*it].get();
         const int32_t cls = class_of(r->prm.S);
+        const bool has_class = s->classes.count(cls) != 0;
+        const int64_t need = r->bytes + (has_class ? 0 : class_fixed_bytes(s->slots_per_class));
+        if (s->used + need > s->budget) {
+            if (++r->passed_over >= kMaxPassOver) break;   // it goes first from now on
+            ++it;
+            continue;
+        }
         int rc = QQA_OK;
         ClassRun *c = get_class(s, cls, &rc);
         if (!c) {
             r->state = QQA_REQ_FAILED;
             r->error = rc;
             r->t_done = now_s();
-            s->queue.pop_front();
+            it = s->queue.erase(it);
             continue;
         }
-        if (std::find(c->slot_req.begin(), c->slot_req.end(), -1) == c->slot_req.end()) break;   // class full
-        s->queue.pop_front();
+        if (std::find(c->slot_req.begin(), c->slot_req.end(), -1) == c->slot_req.end()) {   // class full
+            ++it;
+            continue;
+        }
+        it = s->queue.erase(it);
         s->used += r->bytes;
         rc = qqa_create_problem(r->kind, r->n, r->row_ptr.data(), r->col.empty() ? nullptr : r->col.data(),
                                 r->w.empty() ? nullptr : r->w.data(), s->has_alloc ? &s->alloc : nullptr,

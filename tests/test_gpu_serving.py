@@ -73,10 +73,24 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         alone_srv.close()
 
 
+CLASS_FIXED = 4 * 512 + 8192   # fixed buffers of a class run of 4 slots
+
+
+def _charges(reqs):
+    """Device bytes the server charges each request (read back from a server
+    that only queues them)."""
+    probe = qqa.Server(1 << 40, chunk_steps=30, slots_per_class=4)
+    out = [probe.poll(probe.submit(kind, g, qqa.make_params(p)))["bytes"] for kind, g, p in reqs]
+    probe.close()
+    return out
+
+
 def test_admission_respects_the_hbm_budget_and_rejects_oversize():
     reqs = _requests()
-    sizes = [qqa.request_bytes(g.n, g.nnz, p.S, qqa.FP32) for _, g, p in reqs]
-    budget = max(sizes) + min(sizes)          # the largest and the smallest fit, little else
+    sizes = _charges(reqs)
+    for (kind, g, p), b in zip(reqs, sizes):
+        assert b >= qqa.request_bytes(g.n, g.nnz, p.S, qqa.FP32)   # the estimate leaves out granules and history
+    budget = max(sizes) + min(sizes) + 3 * CLASS_FIXED   # the largest and the smallest fit, little else
     srv = qqa.Server(budget, chunk_steps=30, slots_per_class=4)
     ids = [srv.submit(kind, g, qqa.make_params(p)) for kind, g, p in reqs]
     huge = G.erdos_renyi_avg_degree(50_000, 4.0, 1)
@@ -138,6 +152,45 @@ def test_allocation_failure_fails_only_that_request():
     failed = [s for s in states if s["state"] == qqa.REQ_FAILED]
     assert len(failed) == 1 and failed[0]["error"] == qqa.QQA_ENOMEM
     assert sum(s["state"] == qqa.REQ_DONE for s in states) == 3
-    used, _ = srv.stats()
-    assert used == 0
+    used, classes = srv.stats()
+    assert used == classes * CLASS_FIXED      # only the class runs' fixed buffers remain charged
+    srv.close()
+
+
+def test_device_memory_stays_within_the_budget():
+    """A counting allocator sees every byte the server's runs and graphs take:
+    with a budget that admits only part of a mixed trace at a time, the live
+    bytes never exceed the budget, and every request completes."""
+    import torch
+    live = {"bytes": 0, "peak": 0}
+    sizes_of = {}
+
+    def _alloc(nbytes, stream, ctx):
+        ptr = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        sizes_of[int(ptr)] = int(nbytes)
+        live["bytes"] += int(nbytes)
+        live["peak"] = max(live["peak"], live["bytes"])
+        return ptr
+
+    def _free(ptr, stream, ctx):
+        if ptr:
+            live["bytes"] -= sizes_of.pop(int(ptr))
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    alloc = qqa.qqa_allocator(qqa.ALLOC_FN(_alloc), qqa.FREE_FN(_free), None)
+    reqs = _requests()
+    hub = G.barabasi_albert(3000, 4, 9)       # long rows: their tables and partial sums are charged too
+    reqs.append((MAXCUT, hub, Params(S=64, steps=200, seed=77, lr=1.0, gamma_min=-5.0)))
+    sizes = _charges(reqs)
+    budget = max(sizes) + int(0.3 * (sum(sizes) - max(sizes))) + 3 * CLASS_FIXED
+    srv = qqa.Server(budget, chunk_steps=30, slots_per_class=4, allocator=alloc)
+    ids = [srv.submit(kind, g, qqa.make_params(p)) for kind, g, p in reqs]
+    for _ in range(10_000):
+        r, q, _ = srv.pump()
+        used, _ = srv.stats()
+        assert used <= budget and live["bytes"] <= used
+        if r == 0 and q == 0:
+            break
+    assert all(srv.poll(i)["state"] == qqa.REQ_DONE for i in ids)
+    assert live["peak"] <= budget
     srv.close()

@@ -685,6 +685,9 @@ def run_ours(args):
     if args.workload == "mis_er700_800" and world == 1 and not args.no_subrecords:
         for name in ("maxcut_regular3", "maxcut_ba4"):
             line[name] = workload_record(name, local, stream, alloc, flush)
+        # the serving pattern on a prefix of its fixed seeded trace (the whole
+        # 2000-request trace is --workload serving --serve-requests 2000)
+        line["serving"] = serving_record(args.sub_serve_requests, args.serve_rate, 9, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -694,39 +697,37 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ serving
-def run_serving(args):
+def serving_record(num: int, rate: float, seed: int, local: int):
     """Poisson trace of MIS / max-cut requests through the continuous-batching
-    server; latency from arrival to retirement (host clock), throughput in
-    completed replica-steps per second. Graphs are generated before the clock
-    starts; each request's CSR is submitted (copied) at its arrival time."""
-    import torch
+    server, played twice: at the trace's own rate and at 0.7x the throughput
+    the first play measured (its capacity). Latency is from arrival to
+    retirement (host clock), throughput is completed replica-steps per second
+    of wall time. Graphs are generated before the clock starts; each request's
+    CSR is submitted (copied) at its arrival time."""
     import paper_2409_02135_gb300 as qqa
-    from paper_2409_02135_gb300 import _build
-
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
-    _build.build()
-    world, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    trace = W.serving_trace(num=args.serve_requests, rate_per_s=args.serve_rate, seed=9 + rank)
+    trace = W.serving_trace(num=num, rate_per_s=rate, seed=seed)
     graphs = [W.graph_from_spec(spec) for _, spec, _ in trace]
+    budget = 64 << 30
 
     def play(rate_scale: float):
-        srv = qqa.Server(64 << 30, chunk_steps=50, slots_per_class=64, precision=W.BF16)
+        srv = qqa.Server(budget, chunk_steps=50, slots_per_class=64, precision=W.BF16)
         arrivals = [a / rate_scale for a, _, _ in trace]
         ids = {}
+        live = set()
         nxt = 0
         launches0 = qqa.launch_count()
         t0 = time.perf_counter()
-        done = 0
-        while done < len(trace):
+        while nxt < len(trace) or live:
             now = time.perf_counter() - t0
             while nxt < len(trace) and arrivals[nxt] <= now:
                 spec, p = trace[nxt][1], trace[nxt][2]
                 ids[nxt] = (srv.submit(spec[0], graphs[nxt], qqa.make_params(p)), t0 + arrivals[nxt])
+                live.add(nxt)
                 nxt += 1
-            running, queued, _ = srv.pump() if ids else (0, 0, 0)
-            done = sum(1 for rid, _ in ids.values() if srv.poll(rid)["state"] >= qqa.REQ_DONE)
+            running, queued, finished = srv.pump() if live else (0, 0, 0)
+            if finished or not running:
+                for k in [k for k in live if srv.poll(ids[k][0])["state"] >= qqa.REQ_DONE]:
+                    live.discard(k)
             if running == 0 and queued == 0 and nxt < len(trace):
                 time.sleep(max(0.0, min(0.01, arrivals[nxt] - (time.perf_counter() - t0))))
         wall = time.perf_counter() - t0
@@ -739,7 +740,7 @@ def run_serving(args):
                 rs += trace[k][2].S * trace[k][2].steps
         srv.close()
         lat.sort()
-        return {"rate_per_s": args.serve_rate * rate_scale, "requests": len(trace), "completed": ok,
+        return {"rate_per_s": rate * rate_scale, "requests": len(trace), "completed": ok,
                 "wall_s": wall, "value": rs / wall, "p50_s": lat[len(lat) // 2],
                 "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "gpu_launches": qqa.launch_count() - launches0}
 
@@ -747,15 +748,33 @@ def run_serving(args):
         full = play(1.0)
         # capacity: completed requests per second with the queue always full
         capacity = full["completed"] / full["wall_s"]
-        light = play(0.7 * capacity / args.serve_rate)
-    line = {"metric": METRIC, "value": full["value"], "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
-            "ms_per_step": 1000 * full["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16-storage/f32-math", "data": "synthetic",
-            "config": {"workload": f"serving_poisson{int(args.serve_rate)}_x{len(trace)}",
-                       "requests": "MIS/max-cut, ER avg degree 10, n log-uniform [1e3, 1e6], S in {32..256}, "
-                                   "steps U[1000, 5000]", "budget_bytes": 64 << 30, "chunk_steps": 50},
+        light = play(0.7 * capacity / rate)
+    return {"metric": METRIC, "value": full["value"], "unit": METRIC,
+            "workload": f"serving_poisson{int(rate)}_x{len(trace)}",
+            "requests": "MIS/max-cut, ER avg degree 10, n log-uniform [1e3, 1e6], S in {32..256}, "
+                        "steps U[1000, 5000], BF16", "budget_bytes": budget, "chunk_steps": 50,
             "at_rate": full, "at_0.7x_capacity": light, "clocks": clocks.summary(),
             "gpu_launches": full["gpu_launches"] + light["gpu_launches"]}
+
+
+def run_serving(args):
+    """The serving workload on its own line (--workload serving)."""
+    import torch
+    from paper_2409_02135_gb300 import _build
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU fallback)")
+    _build.build()
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    rec = serving_record(args.serve_requests, args.serve_rate, 9 + rank, local)
+    line = {"metric": METRIC, "value": rec["value"], "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": 1000 * rec["at_rate"]["wall_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-storage/f32-math", "data": "synthetic",
+            "config": {"workload": rec["workload"], "requests": rec["requests"], "budget_bytes": rec["budget_bytes"],
+                       "chunk_steps": rec["chunk_steps"]},
+            "at_rate": rec["at_rate"], "at_0.7x_capacity": rec["at_0.7x_capacity"], "clocks": rec["clocks"],
+            "gpu_launches": rec["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -910,7 +929,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-instance-at-a-time comparison")
     ap.add_argument("--no-subrecords", action="store_true",
                     help="skip the max-cut n = 1e5 records added to the default workload's line")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--sub-serve-requests", type=int, default=64,
+                    help="requests of the serving trace played in the default workload's line")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)

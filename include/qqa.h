@@ -98,9 +98,10 @@ typedef struct qqa_params {
  *                 QQA_KERNEL_STREAM (each thread prefetches the next row's
  *                 slices with cp.async into private shared memory; for
  *                 sparse, memory-bound graphs)
- *                 QQA_KERNEL_DENSE (FP32 runs, S <= 256, dense graphs: the
+ *                 QQA_KERNEL_DENSE (S <= 256, dense graphs: the
  *                 product A.p runs on the tensor cores - tcgen05.mma on an
- *                 fp16 adjacency and two fp16 planes of p, FP32 accumulation
+ *                 fp16 adjacency and two fp16 planes of p (formed from the
+ *                 FP32 state, the master in BF16 runs), FP32 accumulation
  *                 in tensor memory - fused with the rest of the step; needs
  *                 an n_pad^2 fp16 adjacency per instance, n_pad = n rounded
  *                 up to 128; edge weights must be exact in fp16, |w| <= 2048)

@@ -33,7 +33,7 @@ TiledFn step_tiled_kernel_fp32(int G, int VPL, int RPW);
 TiledFn step_tiled_kernel_bf16(int G, int VPL, int RPW);
 StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
 StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
-StepFn step_dense_kernel_fp32(int N);
+StepFn step_dense_kernel(int prec, int N);
 using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
 PipeFn step_pipe_kernel_fp32(int G, int VPL, bool segs);
 PipeFn step_pipe_kernel_bf16(int G, int VPL, bool segs);
@@ -457,10 +457,9 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     r->pipe_seg_fn = nullptr;
     r->hub_fn = nullptr;
     if (mode == QQA_KERNEL_DENSE) {
-        if (r->prec != kFP32) return fail(QQA_EINVAL, "the dense tensor-core step needs an FP32 run");
         const int N = r->S_max_pad <= 64 ? 64 : (r->S_max_pad <= 128 ? 128 : (r->S_max_pad <= 256 ? 256 : 0));
         if (!N) return fail(QQA_EINVAL, "the dense tensor-core step covers at most 256 replicas");
-        r->step_fn = step_dense_kernel_fp32(N);
+        r->step_fn = step_dense_kernel(r->prec, N);
         r->tiled_fn = nullptr;
         r->dense_N = N;
         r->smem = dense_smem_bytes(N);

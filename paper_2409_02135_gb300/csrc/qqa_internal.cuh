@@ -42,7 +42,7 @@ struct __align__(16) InstDesc {
     int32_t *hist_step;          // [hist_cap]
     float4 *scal;                // per-step scalars of the current chunk [kMaxChunk]: x = gamma_t * (-2a),
                                  // y = lr / (1 - b1^(t+1)), z = 1 / sqrt(1 - b2^(t+1))
-    // dense tensor-core path (FP32 runs of dense graphs); null otherwise
+    // dense tensor-core path (dense graphs); null otherwise
     uint16_t *dense_A;           // fp16 adjacency [n_pad][n_pad], zero padded
     uint16_t *dense_XT;          // fp16 state planes [2 buffers][2 (hi, lo)][dense_N][n_pad]: p^t[j][s] at [s][j]
     const void *dense_tmaps;     // 5 TMA tensor maps: adjacency, then planes (buffer 0 hi, lo, buffer 1 hi, lo)

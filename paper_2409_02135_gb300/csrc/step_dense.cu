@@ -1,5 +1,6 @@
 // step_dense.cu -- the fused PQQA step on the 5th-generation tensor cores, for
-// dense graphs (FP32 runs).
+// dense graphs (FP32 runs, and BF16 runs, whose planes come from the FP32
+// master).
 //
 // The sparse product of the step, Y[i][s] = sum_j A_ij p^t[j][s] (Eqs. 22, 24,
 // 26), is a dense contraction when the graph is dense (ER with p = 0.15 has
@@ -18,9 +19,10 @@
 //   - 16 epilogue warps read the accumulator with tcgen05.ld (TMEM lane =
 //     row, column = replica), form the row statistics over the S replicas
 //     through shared memory, and apply the gradient, AdamW, noise and clamp
-//     exactly as the other step kernels do. They write p^{t+1} in FP32 and as
-//     the two transposed fp16 planes for the next step's GEMM (one row per
-//     lane, so the plane writes are coalesced).
+//     exactly as the other step kernels do. They write p^{t+1} (FP32; in BF16
+//     runs the BF16 state and the FP32 master) and, from the FP32 value, the
+//     two transposed fp16 planes for the next step's GEMM (one row per lane,
+//     so the plane writes are coalesced).
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -93,8 +95,9 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n
 
 }  // namespace
 
-// N = MMA width = replicas covered (64, 128 or 256).
-template <int N>
+// N = MMA width = replicas covered (64, 128 or 256); T = replica storage
+// (float, or BF16 with the FP32 master, from which the planes are formed).
+template <typename T, int N>
 __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const InstDesc *__restrict__ descs,
                                                                           const Tile *__restrict__ tiles,
                                                                           const int32_t *__restrict__ num_tiles_p,
@@ -206,8 +209,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
             //    writing the new p back into the same row of B; 3. the fp16 planes
             //    of the new p written transposed from B, consecutive rows per warp.
             constexpr int LD = N + 1;                   // padded row stride: conflict-free columns
-            constexpr int GE = N / 4 >= 32 ? 32 : N / 4;    // lanes per row in the update
-            constexpr int VE = N / 4 >= 32 ? N / 128 : 1;   // 16-byte vectors per lane
+            constexpr int VT = VecT<T>::N;                  // replicas per 16-byte storage vector
+            constexpr int GE = N / VT >= 32 ? 32 : N / VT;  // lanes per row in the update
+            constexpr int VE = N / VT >= 32 ? N / (32 * VT) : 1;   // 16-byte vectors per lane
             constexpr int RPW = 32 / GE;                  // rows per warp at a time
             float *B = reinterpret_cast<float *>(stages);
             const StepCtx c = make_ctx(d, t, r);
@@ -223,13 +227,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                 const int row = tl.row0 + rloc;
                 if (row >= n) continue;   // group-uniform
                 if (c.alpha != 0.0f) {
-                    const float *prow = reinterpret_cast<const float *>(d->X[t & 1]) + (size_t)row * c.S_pad;
-                    float sum = 0.0f, xs[VE][4];
+                    const float *prow = (d->master ? d->master : reinterpret_cast<const float *>(d->X[t & 1])) +
+                                        (size_t)row * c.S_pad;
+                    float sum = 0.0f, xs[VE][VT];
 #pragma unroll
                     for (int v = 0; v < VE; ++v)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int s2 = (v * GE + gl) * 4 + e;
+                        for (int e = 0; e < VT; ++e) {
+                            const int s2 = (v * GE + gl) * VT + e;
                             xs[v][e] = s2 < c.S ? prow[s2] : 0.0f;
                             sum += xs[v][e];
                         }
@@ -238,8 +243,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
 #pragma unroll
                     for (int v = 0; v < VE; ++v)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if ((v * GE + gl) * 4 + e < c.S) {
+                        for (int e = 0; e < VT; ++e)
+                            if ((v * GE + gl) * VT + e < c.S) {
                                 const float dl = xs[v][e] - mean;
                                 sq = fmaf(dl, dl, sq);
                             }
@@ -274,23 +279,23 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
             epi_sync();
             if (acc_ok) {
                 // own rows of p, m, v are loaded one row ahead of the update
-                OwnRow<float, GE, VE> own[2];
+                OwnRow<T, GE, VE> own[2];
                 int rb = warp * RPW;
-                if (tl.row0 + rb + grp < n) load_own<float, GE, VE>(d, c, tl.row0 + rb + grp, gl, own[0]);
+                if (tl.row0 + rb + grp < n) load_own<T, GE, VE>(d, c, tl.row0 + rb + grp, gl, own[0]);
                 for (int it = 0; rb < 128; rb += kDenseEpiWarps * RPW, ++it) {
                     const int rloc = rb + grp;
                     const int row = tl.row0 + rloc;
                     const int nrow = row + kDenseEpiWarps * RPW;
                     if (rb + kDenseEpiWarps * RPW < 128 && nrow < n)
-                        load_own<float, GE, VE>(d, c, nrow, gl, own[(it + 1) & 1]);
+                        load_own<T, GE, VE>(d, c, nrow, gl, own[(it + 1) & 1]);
                     if (row >= n) continue;   // group-uniform
-                    float Y[VE][4];
+                    float Y[VE][VT];
 #pragma unroll
                     for (int v = 0; v < VE; ++v)
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * 4 + e];
+                        for (int e = 0; e < VT; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * VT + e];
                     const float dsum = c.kind == kMaxCut ? rdeg[rloc] : 0.0f;
-                    update_row<float, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, B + rloc * LD,
+                    update_row<T, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, B + rloc * LD,
                                               &rstat[rloc]);
                 }
             }
@@ -325,11 +330,17 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
 
 using StepFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t);
 
-StepFn step_dense_kernel_fp32(int N)
+StepFn step_dense_kernel(int prec, int N)
 {
-    if (N == 64) return qqa_step_dense_kernel<64>;
-    if (N == 128) return qqa_step_dense_kernel<128>;
-    if (N == 256) return qqa_step_dense_kernel<256>;
+    if (prec == kFP32) {
+        if (N == 64) return qqa_step_dense_kernel<float, 64>;
+        if (N == 128) return qqa_step_dense_kernel<float, 128>;
+        if (N == 256) return qqa_step_dense_kernel<float, 256>;
+    } else {
+        if (N == 64) return qqa_step_dense_kernel<__nv_bfloat16, 64>;
+        if (N == 128) return qqa_step_dense_kernel<__nv_bfloat16, 128>;
+        if (N == 256) return qqa_step_dense_kernel<__nv_bfloat16, 256>;
+    }
     return nullptr;
 }
 
@@ -364,7 +375,7 @@ __global__ void dense_planes_kernel(const InstDesc *__restrict__ descs, int32_t 
 {
     const InstDesc &d = descs[slot];
     const int b = d.t & 1;
-    const float *X = reinterpret_cast<const float *>(d.X[b]);
+    const float *X = d.master ? d.master : reinterpret_cast<const float *>(d.X[b]);   // p^t in FP32
     __half *hi = reinterpret_cast<__half *>(d.dense_XT) + (size_t)b * 2 * d.dense_N * d.n_pad;
     __half *lo = hi + (size_t)d.dense_N * d.n_pad;
     const long long total = (long long)d.n * d.S_pad;

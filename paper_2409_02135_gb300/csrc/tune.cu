@@ -76,7 +76,7 @@ extern "C" int qqa_autotune(qqa_problem *const *problems, const qqa_params *para
     if (S_max == 1) {   // one replica per instance: the scalar kernel, lanes per row x block size
         for (int L : {4, 8, 16, 32})
             for (int bt : {128, 256}) cands.push_back(qqa_launch_config{0, 0, bt, 0, 1, QQA_KERNEL_SCALAR, L, 0});
-    } else if (params[0].precision == QQA_FP32 && S_max <= 256 && n_max <= 8192) {   // tensor-core step (fp16 adjacency)
+    } else if (S_max <= 256 && n_max <= 8192) {   // tensor-core step (fp16 adjacency)
         cands.push_back(qqa_launch_config{0, 0, 0, 0, 1, QQA_KERNEL_DENSE, 0, 0});
     }
     for (int G = 1; G <= 32 && S_max > 1; G *= 2)

@@ -135,9 +135,7 @@ def test_single_step_at_schedule_endpoints(kind, prec, kernel):
     """The schedule's ends (App. C.2): the last step t = K - 1, where gamma_t =
     gamma_max > 0 (the regime that drives p to integral points), from an interior
     state with warm moments; and a one-step schedule K = 1 (gamma_0 = gamma_min)
-    from the initial draw. Direct, pipelined and tensor-core steps (FP32 only)."""
-    if kernel == qqa.KERNEL_DENSE and prec == BF16:
-        pytest.skip("the tensor-core step runs FP32 states")
+    from the initial draw. Direct, pipelined and tensor-core steps."""
     g = _graph(kind, 200, 0.5 if kind == MAXCLIQUE else (0.2 if kernel == qqa.KERNEL_DENSE else 0.05), 90 + kind,
                weighted=(kind == MAXCUT))
     cfg = qqa.LaunchConfig(kernel=kernel)
@@ -311,20 +309,23 @@ def test_stream_kernel_single_step_parity_sparse_graph():
     _check_step(MAXCUT, g, p, BF16, run)
 
 
+@pytest.mark.parametrize("prec", [FP32, BF16])
 @pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
 @pytest.mark.parametrize("n,p_edge,S", [(750, 0.15, 128), (300, 0.2, 64), (129, 0.3, 100), (450, 0.1, 200)])
-def test_dense_tensor_core_step_matches_oracle(kind, n, p_edge, S):
-    """tcgen05 step (fp16 adjacency, two fp16 planes of p, FP32 accumulation in
-    TMEM): single steps from the same state as the oracle, cold and warm
-    moments, ragged last tile, several K chunks, MMA widths 64/128/256."""
+def test_dense_tensor_core_step_matches_oracle(kind, n, p_edge, S, prec):
+    """tcgen05 step (fp16 adjacency, two fp16 planes of p - from the FP32
+    master in BF16 runs - FP32 accumulation in TMEM): single steps from the
+    same state as the oracle, cold and warm moments, ragged last tile, several
+    K chunks, MMA widths 64/128/256."""
     g = _graph(kind, n, p_edge if kind != MAXCLIQUE else 0.5, 60 + kind, weighted=(kind == MAXCUT))
-    p = Params(S=S, steps=300, alpha_comm=0.3, lr=1.0, seed=8, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    p = Params(S=S, steps=300, alpha_comm=0.3, lr=1.0, seed=8, gamma_min=-5.0 if kind == MAXCUT else -2.0,
+               precision=prec)
     run = make_run(kind, g, p, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
     c = run.config()
     assert c.kernel == qqa.KERNEL_DENSE and c.kernel_param in (64, 128, 256)
-    _check_step(kind, g, p, FP32, run)
+    _check_step(kind, g, p, prec, run)
     run.steps(40)
-    _check_step(kind, g, p, FP32, run)
+    _check_step(kind, g, p, prec, run)
 
 
 def test_dense_step_follows_the_direct_step_and_resumes():
@@ -484,10 +485,11 @@ def test_round_eval_is_exact(kind, prec):
             assert (o, f) == (want.obj[want.best], True)
 
 
+@pytest.mark.parametrize("prec", [FP32, BF16])
 @pytest.mark.parametrize("kind", [MIS, MAXCUT, MAXCLIQUE])
 @pytest.mark.parametrize("n,p_edge,S,weighted", [(300, 0.15, 128, False), (1100, 0.05, 100, False),
                                                  (257, 0.3, 37, False), (200, 0.1, 64, True)])
-def test_round_eval_on_the_tensor_core_step_is_exact(kind, n, p_edge, S, weighted):
+def test_round_eval_on_the_tensor_core_step_is_exact(kind, n, p_edge, S, weighted, prec):
     """Tensor-core runs of unit-weight graphs count costs by popcount over
     adjacency and replica bitsets (weighted ones by the per-edge kernel): costs,
     feasibility, energies and the best replica equal the oracle's evaluation of
@@ -495,7 +497,7 @@ def test_round_eval_on_the_tensor_core_step_is_exact(kind, n, p_edge, S, weighte
     S = 37 leave ragged words."""
     weighted = weighted and kind == MAXCUT
     g = _graph(kind, n, p_edge, 60 + kind, weighted=weighted)
-    prm = Params(S=S, steps=200, seed=5, precision=FP32, gamma_min=-5.0 if kind == MAXCUT else -2.0)
+    prm = Params(S=S, steps=200, seed=5, precision=prec, gamma_min=-5.0 if kind == MAXCUT else -2.0)
     run = make_run(kind, g, prm, config=qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE))
     assert run.config().kernel == qqa.KERNEL_DENSE
     for k in (41, 120):

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libqqa.so")
 UNITS = ["step_direct_fp32.cu", "step_direct_bf16.cu", "step_tiled_fp32.cu", "step_tiled_bf16.cu",
          "step_stream_fp32.cu", "step_stream_bf16.cu", "aux_kernels.cu", "api.cu", "eval_noalloc.cu", "tune.cu",
          "server.cu", "step_dense.cu", "step_pipe_fp32.cu", "step_pipe_bf16.cu", "color.cu",
-         "step_hub_fp32.cu", "step_hub_bf16.cu", "step_scalar.cu"]
+         "step_hub_fp32.cu", "step_hub_bf16.cu", "step_scalar.cu", "step_dense_update.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

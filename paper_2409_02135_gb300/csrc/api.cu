@@ -33,14 +33,16 @@ TiledFn step_tiled_kernel_fp32(int G, int VPL, int RPW);
 TiledFn step_tiled_kernel_bf16(int G, int VPL, int RPW);
 StepFn step_stream_kernel_fp32(int G, int VPL, int NB);
 StepFn step_stream_kernel_bf16(int G, int VPL, int NB);
-StepFn step_dense_kernel(int prec, int N);
+StepFn dense_gemm_kernel(int N);
+using UpdFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
+UpdFn dense_update_kernel(int prec, int G, int VPL);
 using PipeFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t, int32_t);
 PipeFn step_pipe_kernel_fp32(int G, int VPL, bool segs);
 PipeFn step_pipe_kernel_bf16(int G, int VPL, bool segs);
 StepFn step_hub_kernel_fp32(int G, int VPL);
 StepFn step_hub_kernel_bf16(int G, int VPL);
 StepFn step_scalar_kernel(int prec, int L);
-int dense_threads();
+int dense_gemm_threads();
 int dense_smem_bytes(int N);
 }  // namespace qqa
 
@@ -339,6 +341,10 @@ struct qqa_run {
     int32_t kernels_per_step = 1;
     bool dynamic = false;             // slots come and go: always launch the full persistent grid
     int32_t dense_N = 0;              // > 0: tensor-core step (MMA width = replicas covered)
+    UpdFn upd_fn = nullptr;           // its update kernel (32-row tiles of the second list)
+    int32_t upd_block = 256, upd_max_grid = 0, upd_smem = 0, upd_ld = 0;
+    Tile *d_tiles2 = nullptr;         // the update kernel's tiles
+    int32_t tile2_cap = 0, num_tiles2 = 0;
     TiledFn tiled_fn = nullptr;       // set when the TMA-staged kernel is used
     PipeFn pipe_fn = nullptr;         // set when the pipelined kernel is used
     PipeFn pipe_seg_fn = nullptr;     // its variant that also takes segment work items of long rows
@@ -404,6 +410,7 @@ static int resolve_scalar(qqa_run *r, qqa_launch_config c)
     r->pipe_fn = nullptr;
     r->pipe_seg_fn = nullptr;
     r->hub_fn = nullptr;
+    r->upd_fn = nullptr;
     r->dense_N = 0;
     r->smem = 0;
     r->rows_per_tile = block;   // 32 rows per warp
@@ -459,20 +466,35 @@ static int resolve_config(qqa_run *r, const qqa_launch_config *cfg, int staged_h
     if (mode == QQA_KERNEL_DENSE) {
         const int N = r->S_max_pad <= 64 ? 64 : (r->S_max_pad <= 128 ? 128 : (r->S_max_pad <= 256 ? 256 : 0));
         if (!N) return fail(QQA_EINVAL, "the dense tensor-core step covers at most 256 replicas");
-        r->step_fn = step_dense_kernel(r->prec, N);
+        r->step_fn = dense_gemm_kernel(N);
         r->tiled_fn = nullptr;
         r->dense_N = N;
         r->smem = dense_smem_bytes(N);
-        const int block_d = dense_threads();
-        int dev = 0, sms = 0, occ = 0;
+        const int block_d = dense_gemm_threads();
+        int dev = 0, sms = 0, occ = 0, occ_u = 0;
         QQA_CK(cudaGetDevice(&dev));
         QQA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         QQA_CK(cudaFuncSetAttribute(r->step_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem));
         QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, r->step_fn, block_d, r->smem));
         if (occ < 1) return fail(QQA_EINVAL, "dense step kernel does not fit on an SM");
+        // the update kernel: up to 16 replicas per lane (the epilogue's
+        // per-row work is shared by more elements), as many lanes as cover S
+        int32_t Vu = 16 / r->vec;   // 4 FP32 or 2 BF16 vectors
+        int32_t nvec = 1;
+        while (nvec * r->vec < r->S_max_pad) nvec <<= 1;
+        Vu = std::min(Vu, nvec);
+        const int32_t Gu = nvec / Vu;
+        r->upd_fn = dense_update_kernel(r->prec, Gu, Vu);
+        if (!r->upd_fn) return fail(QQA_EINVAL, "no tensor-core update kernel for G=%d VPL=%d", Gu, Vu);
+        r->upd_ld = r->S_max_pad + 1;   // odd row stride of the shared buffer: conflict-free transposition
+        r->upd_smem = 32 * r->upd_ld * (int)sizeof(float);
+        QQA_CK(cudaFuncSetAttribute(r->upd_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, r->upd_smem));
+        QQA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, r->upd_fn, r->upd_block, r->upd_smem));
+        if (occ_u < 1) return fail(QQA_EINVAL, "dense update kernel does not fit on an SM");
+        r->upd_max_grid = sms * occ_u;
         r->rows_per_tile = 128;
-        c.group_lanes = 32;
-        c.vec_per_lane = 1;
+        c.group_lanes = Gu;
+        c.vec_per_lane = Vu;
         c.block_threads = block_d;
         c.kernel = mode;
         c.kernel_param = N;
@@ -648,6 +670,29 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
         drop_graphs(r);  // captured graphs hold the old tile pointer
     }
     if (nt) QQA_CK(cudaMemcpyAsync(r->d_tiles, tiles.data(), sizeof(Tile) * (size_t)nt, cudaMemcpyHostToDevice, st));
+    // tensor-core runs: the update kernel's 32-row tiles
+    int32_t nt2 = 0;
+    if (r->dense_N) {
+        std::vector<Tile> t2;
+        for (int32_t k = 0; k < r->capacity; ++k) {
+            const SlotHost &s = r->slots[k];
+            if (!s.active) continue;
+            for (int32_t row0 = 0; row0 < s.n; row0 += 32) t2.push_back(Tile{k, row0});
+        }
+        nt2 = (int32_t)t2.size();
+        if (nt2 > r->tile2_cap || (r->tile2_cap > 256 && nt2 < r->tile2_cap / 4)) {
+            const int32_t cap = nt2 > r->tile2_cap ? std::max<int32_t>(nt2, 2 * r->tile2_cap) : std::max(2 * nt2, 256);
+            QQA_CK(cudaStreamSynchronize(st));
+            Tile *buf = (Tile *)r->alloc.get(sizeof(Tile) * (size_t)cap, st);
+            if (!buf) return fail(QQA_ENOMEM, "tile list allocation failed");
+            r->alloc.put(r->d_tiles2, st);
+            r->d_tiles2 = buf;
+            r->tile2_cap = cap;
+            drop_graphs(r);
+        }
+        if (nt2) QQA_CK(cudaMemcpyAsync(r->d_tiles2, t2.data(), sizeof(Tile) * (size_t)nt2, cudaMemcpyHostToDevice, st));
+    }
+    r->num_tiles2 = nt2;
     // long-row work items (one per segment) and the max-clique slots
     std::vector<Tile> hub;
     std::vector<int32_t> cliques;
@@ -691,7 +736,7 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     r->hub_grid = hub_grid;
     r->num_hub_items = nh;
     r->num_clique = nc;
-    r->kernels_per_step = 1 + (nh ? 1 : 0) + (nc ? 1 : 0);
+    r->kernels_per_step = 1 + (r->upd_fn ? 1 : 0) + (nh ? 1 : 0) + (nc ? 1 : 0);
     // second word: the run's replica state (p^t, p^{t+1}, master, m, v) is larger
     // than most of L2, so streaming kernels mark it evict-first
     double state_bytes = 0.0;
@@ -704,6 +749,7 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     r->tile_words[0] = nt;
     r->tile_words[1] = state_bytes > 0.75 * (double)l2 ? 1 : 0;
     r->tile_words[2] = nh;
+    r->tile_words[3] = nt2;
     QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
     r->num_tiles = nt;
@@ -832,12 +878,14 @@ static int setup_dense_slot(qqa_run *r, int32_t k, InstDesc &d, std::vector<void
     d.dense_N = N;
     d.dense_A = (uint16_t *)r->alloc.get(a_bytes, st);
     d.dense_XT = (uint16_t *)r->alloc.get(x_bytes, st);
+    d.dense_Y = (float *)r->alloc.get((size_t)d.n * r->slots[k].S_pad * sizeof(float), st);
     void *tm = r->alloc.get(5 * sizeof(CUtensorMap), st);
     if (d.dense_A) dev.push_back(d.dense_A);
     if (d.dense_XT) dev.push_back(d.dense_XT);
+    if (d.dense_Y) dev.push_back(d.dense_Y);
     if (tm) dev.push_back(tm);
-    if (!d.dense_A || !d.dense_XT || !tm) return fail(QQA_ENOMEM, "dense adjacency of %lld x %lld fp16 does not fit",
-                                                     (long long)n_pad, (long long)n_pad);
+    if (!d.dense_A || !d.dense_XT || !d.dense_Y || !tm)
+        return fail(QQA_ENOMEM, "dense adjacency of %lld x %lld fp16 does not fit", (long long)n_pad, (long long)n_pad);
     // unit-weight graphs: adjacency and rounded replicas as bitsets, so the
     // evaluation counts by popcount
     d.dense_Abits = nullptr;
@@ -1243,6 +1291,7 @@ extern "C" void qqa_run_destroy(qqa_run *r)
     r->alloc.put(r->d_descs, 0);
     r->alloc.put(r->d_tiles, 0);
     r->alloc.put(r->d_hub_items, 0);
+    r->alloc.put(r->d_tiles2, 0);
     r->alloc.put(r->d_clique_slots, 0);
     r->alloc.put(r->d_num_tiles, 0);
     r->alloc.put(r->d_status, 0);
@@ -1273,6 +1322,11 @@ static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream
         else
             r->step_fn<<<grid, r->cfg.block_threads, r->smem, st>>>(r->d_descs, r->d_tiles, r->d_num_tiles,
                                                                     r->d_status, i);
+        if (r->upd_fn) {   // tensor-core step: the update of every row after the product
+            const int32_t g2 = r->dynamic ? r->upd_max_grid : std::max(1, std::min(r->upd_max_grid, r->num_tiles2));
+            r->upd_fn<<<g2, r->upd_block, r->upd_smem, st>>>(r->d_descs, r->d_tiles2, r->d_num_tiles + 3, r->d_status,
+                                                             i, r->upd_ld);
+        }
         if (r->num_hub_items > 0)   // long rows of the same step (disjoint rows, same p^t)
             r->hub_fn<<<r->hub_grid, 256, 0, st>>>(r->d_descs, r->d_hub_items, r->d_num_tiles + 2, r->d_status, i);
         if (r->num_clique > 0)      // column sums of p^{t+1} for the next step's Eq. 24 term

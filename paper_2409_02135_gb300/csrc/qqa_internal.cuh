@@ -48,6 +48,8 @@ struct __align__(16) InstDesc {
     const void *dense_tmaps;     // 5 TMA tensor maps: adjacency, then planes (buffer 0 hi, lo, buffer 1 hi, lo)
     uint32_t *dense_Abits;       // unit-weight graphs: adjacency bitsets [n_pad][n_pad / 32] (bit j of row i = A_ij)
     uint32_t *dense_xbits;       // rounded replicas as node bitsets [S rounded to 32][n_pad / 32]
+    float *dense_Y;              // the tensor cores' product A.p^t [n][S_pad] (FP32), read by the update
+    const void *pad_ptr2;
     int32_t n_pad, dense_N;
     int32_t long_thresh;         // rows with more neighbours than this are long (INT32_MAX: none)
     int32_t hub_active;          // 1: the step kernels leave long rows to the segment work items

@@ -32,10 +32,9 @@ namespace qqa {
 
 namespace {
 
-// pipeline depth: three stages up to N = 128, two at N = 256 (80 KB per stage)
-__host__ __device__ constexpr int dense_stages(int N) { return N >= 256 ? 2 : 3; }
-constexpr int kDenseEpiWarps = 16;
-constexpr int kDenseThreads = (kDenseEpiWarps + 1) * 32;
+// pipeline depth: four stages up to N = 128 (48 KB each), two at N = 256 (80 KB each)
+__host__ __device__ constexpr int dense_stages(int N) { return N >= 256 ? 2 : 4; }
+constexpr int kGemmThreads = 6 * 32;   // warps 0-3: accumulator -> Y; warp 4: TMA loads; warp 5: MMAs
 
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
 {
@@ -91,22 +90,28 @@ __device__ __forceinline__ bool mbar_wait_limit(uint32_t mbar, uint32_t parity)
     }
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kDenseEpiWarps * 32) : "memory"); }
-
 }  // namespace
 
-// N = MMA width = replicas covered (64, 128 or 256); T = replica storage
-// (float, or BF16 with the FP32 master, from which the planes are formed).
-template <typename T, int N>
-__global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const InstDesc *__restrict__ descs,
-                                                                          const Tile *__restrict__ tiles,
-                                                                          const int32_t *__restrict__ num_tiles_p,
-                                                                          RunStatus *__restrict__ status, int32_t r)
+// ---------------------------------------------------------------------------
+// Product kernel: Y = A p^t for 128 rows of one instance per tile. Warp 4's
+// first lane streams 64-wide K chunks of the fp16 adjacency and of both fp16
+// planes of p^t with TMA, warp 5's first lane issues tcgen05.mma on them (M =
+// 128, N = the MMA width, K = 16; hi and lo accumulate into the same FP32
+// accumulator); warps 0-3 read
+// the accumulator (TMEM lane = row, column = replica) and store Y[row][s] for
+// the update kernel. N = MMA width (64, 128 or 256 replicas). The loads and
+// the MMAs are issued by two different warps, so the tensor cores take each
+// chunk as soon as it lands while the loads run up to four stages ahead.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kGemmThreads, 1) qqa_dense_gemm_kernel(const InstDesc *__restrict__ descs,
+                                                                         const Tile *__restrict__ tiles,
+                                                                         const int32_t *__restrict__ num_tiles_p,
+                                                                         RunStatus *__restrict__ status, int32_t r)
 {
     constexpr int A_BYTES = 128 * 128;       // 128 rows x 64 fp16
     constexpr int B_BYTES = N * 128;         // N rows x 64 fp16
     constexpr int STAGE = A_BYTES + 2 * B_BYTES;
-    constexpr int CPT = N / 4;               // replica columns per epilogue thread
     constexpr int kDenseStages = dense_stages(N);
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)dsm_raw + 1023) & ~(uintptr_t)1023);
@@ -115,10 +120,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
     uint64_t *mb_empty = mb_full + kDenseStages;
     uint64_t *mb_acc = mb_empty + kDenseStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mb_acc + 1);
-    float *red = reinterpret_cast<float *>(tmem_slot + 4);   // [4][128] scratch (unused)
-    float *csum = red + 4 * 128;                              // [N] scratch (unused)
-    float2 *rstat = reinterpret_cast<float2 *>(csum + N);     // [128] row mean, 1/STD (Eq. 10)
-    float *rdeg = reinterpret_cast<float *>(rstat + 128);     // [128] weighted degree (max-cut)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_tiles = *num_tiles_p;
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    uint32_t chunk_base = 0;   // K chunks this CTA has streamed so far (control thread)
+    uint32_t chunk_base = 0;   // K chunks this CTA has streamed so far (producer and MMA warps)
     uint32_t tiles_done = 0;   // accumulator phases completed (all threads)
     bool failed = false;
 
@@ -153,22 +154,22 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
         if (t >= d->K) continue;   // block-uniform
         const int n = d->n, n_pad = d->n_pad, nK = n_pad / 64;
 
-        if (warp == kDenseEpiWarps) {
+        if (warp == 4) {
             if (lane == 0) {
-                // ---------------- control thread: TMA + MMA pipeline ----------------
+                // ---------------- producer: TMA loads of the K chunks ----------------
                 const CUtensorMap *tm = reinterpret_cast<const CUtensorMap *>(d->dense_tmaps);
                 const CUtensorMap *tmA = tm, *tmH = tm + 1 + 2 * (t & 1), *tmL = tmH + 1;
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA) : "memory");
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmH) : "memory");
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmL) : "memory");
-                const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-                bool ok = true;
-                auto fill = [&](int kc) {
+                for (int kc = 0; kc < nK; ++kc) {
                     const uint32_t f = chunk_base + kc;
                     const int st = f % kDenseStages;
-                    if (f >= kDenseStages)
-                        ok = ok && mbar_wait_limit(smem_addr(mb_empty + st), ((f / kDenseStages) - 1) & 1);
-                    if (!ok) return;
+                    // the stage is free once the MMAs that read it last have completed
+                    if (f >= kDenseStages && !mbar_wait_limit(smem_addr(mb_empty + st), ((f / kDenseStages) - 1) & 1)) {
+                        atomicAdd(&status->timeouts, 1ULL);
+                        break;
+                    }
                     unsigned char *sp = stages + st * STAGE;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mb_full + st)),
                                  "r"(STAGE)
@@ -176,9 +177,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                     tma_load_2d(smem_addr(sp), tmA, 64 * kc, tl.row0, smem_addr(mb_full + st));
                     tma_load_2d(smem_addr(sp + A_BYTES), tmH, 64 * kc, 0, smem_addr(mb_full + st));
                     tma_load_2d(smem_addr(sp + A_BYTES + B_BYTES), tmL, 64 * kc, 0, smem_addr(mb_full + st));
-                };
-                for (int kc = 0; kc < kDenseStages && kc < nK; ++kc) fill(kc);
-                for (int kc = 0; kc < nK && ok; ++kc) {
+                }
+            }
+            __syncwarp();
+            chunk_base += nK;
+        } else if (warp == 5) {
+            if (lane == 0) {
+                // ---------------- MMA issuer: one chunk after the other as they land ----------------
+                const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+                bool ok = true;
+                for (int kc = 0; kc < nK; ++kc) {
                     const uint32_t c = chunk_base + kc;
                     const int st = c % kDenseStages;
                     ok = mbar_wait_limit(smem_addr(mb_full + st), (c / kDenseStages) & 1);
@@ -194,131 +202,41 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
                         mma_f16(tmem, ad, bl, idesc, 1u);
                     }
                     mma_commit(smem_addr(mb_empty + st));   // stage free once these MMAs are done
-                    if (kc + kDenseStages < nK) fill(kc + kDenseStages);
                 }
-                chunk_base += nK;
                 if (ok) mma_commit(smem_addr(mb_acc));     // accumulator complete
                 else atomicAdd(&status->timeouts, 1ULL);
             }
             __syncwarp();
+            chunk_base += nK;
         } else {
-            // ---------------- 16 epilogue warps ----------------
-            // 1. accumulator (TMEM lane = row) -> shared buffer B[128][N + 1] in the
-            //    now idle stage area; 2. coalesced row-group update (lanes over
-            //    replicas, as in the other step kernels) reading Y from B and
-            //    writing the new p back into the same row of B; 3. the fp16 planes
-            //    of the new p written transposed from B, consecutive rows per warp.
-            constexpr int LD = N + 1;                   // padded row stride: conflict-free columns
-            constexpr int VT = VecT<T>::N;                  // replicas per 16-byte storage vector
-            constexpr int GE = N / VT >= 32 ? 32 : N / VT;  // lanes per row in the update
-            constexpr int VE = N / VT >= 32 ? N / (32 * VT) : 1;   // 16-byte vectors per lane
-            constexpr int RPW = 32 / GE;                  // rows per warp at a time
-            float *B = reinterpret_cast<float *>(stages);
-            const StepCtx c = make_ctx(d, t, r);
-            const int q = warp & 3, cg = warp >> 2;
-            const int rl = 32 * q + lane;
-            const int col0 = cg * CPT;
-            const int gl = lane & (GE - 1), grp = lane / GE;
-            const unsigned gmask = (GE == 32) ? 0xffffffffu : (((1u << GE) - 1u) << (grp * GE));
-            // while the tensor cores run: row statistics of p^t and max-cut degrees
-            // (they do not depend on the product)
-            for (int rb = warp * RPW; rb < 128; rb += kDenseEpiWarps * RPW) {
-                const int rloc = rb + grp;
-                const int row = tl.row0 + rloc;
-                if (row >= n) continue;   // group-uniform
-                if (c.alpha != 0.0f) {
-                    const float *prow = (d->master ? d->master : reinterpret_cast<const float *>(d->X[t & 1])) +
-                                        (size_t)row * c.S_pad;
-                    float sum = 0.0f, xs[VE][VT];
-#pragma unroll
-                    for (int v = 0; v < VE; ++v)
-#pragma unroll
-                        for (int e = 0; e < VT; ++e) {
-                            const int s2 = (v * GE + gl) * VT + e;
-                            xs[v][e] = s2 < c.S ? prow[s2] : 0.0f;
-                            sum += xs[v][e];
-                        }
-                    const float mean = group_sum<GE>(sum, gmask) * c.inv_S;
-                    float sq = 0.0f;
-#pragma unroll
-                    for (int v = 0; v < VE; ++v)
-#pragma unroll
-                        for (int e = 0; e < VT; ++e)
-                            if ((v * GE + gl) * VT + e < c.S) {
-                                const float dl = xs[v][e] - mean;
-                                sq = fmaf(dl, dl, sq);
-                            }
-                    const float istd = rsqrt_ftz(group_sum<GE>(sq, gmask) * c.inv_S + c.comm_eps);
-                    if (gl == 0) rstat[rloc] = make_float2(mean, istd);
-                }
-                if (c.kind == kMaxCut) {
-                    const int k0 = __ldg(d->row_ptr + row), k1 = __ldg(d->row_ptr + row + 1);
-                    float ds = 0.0f;
-                    if (d->w) {
-                        for (int k = k0 + gl; k < k1; k += GE) ds += (float)__ldg(d->w + k);
-                        ds = group_sum<GE>(ds, gmask);
-                    } else {
-                        ds = (float)(k1 - k0);
-                    }
-                    if (gl == 0) rdeg[rloc] = ds;
-                }
-            }
+            // ---------------- warps 0-3: accumulator -> Y ----------------
             const bool acc_ok = mbar_wait_limit(smem_addr(mb_acc), tiles_done & 1);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!acc_ok) {
                 if (threadIdx.x == 0) atomicAdd(&status->timeouts, 1ULL);
+                failed = true;
             } else {
+                const int row = tl.row0 + 32 * warp + lane;   // TMEM lane = row of the tile
+                const int S_pad = d->S_pad;
+                float *yrow = d->dense_Y + (size_t)row * S_pad;
 #pragma unroll 1
-                for (int c16 = 0; c16 < CPT; c16 += 16) {
+                for (int c16 = 0; c16 < N && c16 < S_pad; c16 += 16) {
                     uint32_t yr[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(col0 + c16), yr);
+                    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c16, yr);
+                    if (row < n) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) B[rl * LD + col0 + c16 + e] = __uint_as_float(yr[e]);
-                }
-            }
-            epi_sync();
-            if (acc_ok) {
-                // own rows of p, m, v are loaded one row ahead of the update
-                OwnRow<T, GE, VE> own[2];
-                int rb = warp * RPW;
-                if (tl.row0 + rb + grp < n) load_own<T, GE, VE>(d, c, tl.row0 + rb + grp, gl, own[0]);
-                for (int it = 0; rb < 128; rb += kDenseEpiWarps * RPW, ++it) {
-                    const int rloc = rb + grp;
-                    const int row = tl.row0 + rloc;
-                    const int nrow = row + kDenseEpiWarps * RPW;
-                    if (rb + kDenseEpiWarps * RPW < 128 && nrow < n)
-                        load_own<T, GE, VE>(d, c, nrow, gl, own[(it + 1) & 1]);
-                    if (row >= n) continue;   // group-uniform
-                    float Y[VE][VT];
-#pragma unroll
-                    for (int v = 0; v < VE; ++v)
-#pragma unroll
-                        for (int e = 0; e < VT; ++e) Y[v][e] = B[rloc * LD + (v * GE + gl) * VT + e];
-                    const float dsum = c.kind == kMaxCut ? rdeg[rloc] : 0.0f;
-                    update_row<T, GE, VE>(d, c, row, gl, gmask, Y, dsum, own[it & 1], status, B + rloc * LD,
-                                              &rstat[rloc]);
-                }
-            }
-            epi_sync();
-            if (acc_ok) {
-                __half *XTn = reinterpret_cast<__half *>(d->dense_XT) + (size_t)((t + 1) & 1) * 2 * d->dense_N * n_pad;
-                __half *XTn_lo = XTn + (size_t)d->dense_N * n_pad;
-                const int j = threadIdx.x & 127;   // row within the tile: consecutive across a warp
-                const int row = tl.row0 + j;
-                if (row < n)
-                    for (int s2 = threadIdx.x >> 7; s2 < c.S_pad; s2 += kDenseEpiWarps * 32 / 128) {
-                        const float pv = B[j * LD + s2];
-                        const __half hi = __float2half_rn(pv);
-                        XTn[(size_t)s2 * n_pad + row] = hi;
-                        XTn_lo[(size_t)s2 * n_pad + row] = __float2half_rn(pv - __half2float(hi));
+                        for (int e = 0; e < 16; e += 4)
+                            if (c16 + e < S_pad)
+                                *reinterpret_cast<float4 *>(yrow + c16 + e) =
+                                    make_float4(__uint_as_float(yr[e]), __uint_as_float(yr[e + 1]),
+                                                __uint_as_float(yr[e + 2]), __uint_as_float(yr[e + 3]));
                     }
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            if (!acc_ok) failed = true;
         }
         ++tiles_done;
-        __syncthreads();   // the accumulator is reused by the next tile
-        failed = __syncthreads_or(failed);
+        failed = __syncthreads_or(failed);   // the accumulator is reused by the next tile
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     __syncthreads();
@@ -330,27 +248,21 @@ __global__ void __launch_bounds__(kDenseThreads, 1) qqa_step_dense_kernel(const 
 
 using StepFn = void (*)(const InstDesc *, const Tile *, const int32_t *, RunStatus *, int32_t);
 
-StepFn step_dense_kernel(int prec, int N)
+StepFn dense_gemm_kernel(int N)
 {
-    if (prec == kFP32) {
-        if (N == 64) return qqa_step_dense_kernel<float, 64>;
-        if (N == 128) return qqa_step_dense_kernel<float, 128>;
-        if (N == 256) return qqa_step_dense_kernel<float, 256>;
-    } else {
-        if (N == 64) return qqa_step_dense_kernel<__nv_bfloat16, 64>;
-        if (N == 128) return qqa_step_dense_kernel<__nv_bfloat16, 128>;
-        if (N == 256) return qqa_step_dense_kernel<__nv_bfloat16, 256>;
-    }
+    if (N == 64) return qqa_dense_gemm_kernel<64>;
+    if (N == 128) return qqa_dense_gemm_kernel<128>;
+    if (N == 256) return qqa_dense_gemm_kernel<256>;
     return nullptr;
 }
 
-int dense_threads() { return kDenseThreads; }
+int dense_gemm_threads() { return kGemmThreads; }
 
 int dense_smem_bytes(int N)
 {
     const int stage = 128 * 128 + 2 * N * 128;
     const int ns = dense_stages(N);
-    return 1024 + ns * stage + (2 * ns + 1) * 8 + 16 + 4 * 128 * 4 + N * 4 + 128 * 8 + 128 * 4 + 64;
+    return 1024 + ns * stage + (2 * ns + 1) * 8 + 16 + 64;
 }
 
 // ---------------------------------------------------------------------------

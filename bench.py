@@ -930,7 +930,7 @@ def main():
     ap.add_argument("--no-subrecords", action="store_true",
                     help="skip the max-cut n = 1e5 records added to the default workload's line")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--sub-serve-requests", type=int, default=64,
+    ap.add_argument("--sub-serve-requests", type=int, default=32,
                     help="requests of the serving trace played in the default workload's line")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

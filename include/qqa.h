@@ -420,8 +420,10 @@ void qqa_server_destroy(qqa_server *s);
  * loads the library holds until exit; n * ceil(S/32) must not exceed 1048576,
  * else QQA_EINVAL. Every call shares that array, so calls whose work overlaps
  * on the GPU race. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture begins. Error messages: qqa_noalloc_last_error().
+ * address (cudaGetSymbolAddress) and keeps it for that device's CUDA context;
+ * a call in a new context (after cudaDeviceReset, say) looks it up again.
+ * Make a call that looks the address up before any stream capture begins.
+ * Error messages: qqa_noalloc_last_error().
  */
 int qqa_round_eval_noalloc(int32_t kind, int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col,
                            const int32_t *w, int32_t S, int64_t ld, const float *X, float lambda, int64_t *obj,

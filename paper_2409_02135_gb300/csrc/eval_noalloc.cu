@@ -18,12 +18,17 @@
 // Host code cannot use the array's name as a device address (in host code it
 // names a host-side stand-in), so the first call on each device asks the
 // runtime for the device address with cudaGetSymbolAddress, with that device
-// current, and caches it. That first call on a device should come before any
-// stream capture begins.
+// current, and caches it together with the identity of the CUDA context it
+// belongs to: after cudaDeviceReset the device gets a new context (and the
+// library image a new address), and the next call looks the address up again
+// instead of using the stale one. A call that looks the address up should
+// come before any stream capture begins.
 #include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <string>
+
+#include <cuda.h>
 
 #include "../../include/qqa.h"
 
@@ -42,6 +47,32 @@ __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 std::mutex g_mu;
 NoAllocScratch *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // unique id of the context the address is valid in
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// looked up through the runtime, so the library needs no link to libcuda).
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+        (void)cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 thread_local std::string g_noalloc_error;
 
@@ -189,7 +220,11 @@ extern "C" int qqa_round_eval_noalloc(int32_t kind, int32_t n, int64_t nnz, cons
     NoAllocScratch *sc = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {
+        unsigned long long ctx_id = 0;
+        if (!g_scratch_addr[dev] || !current_context_id(&ctx_id) || ctx_id != g_scratch_ctx[dev]) {
+            // first call on this device, or its context changed (or cannot be
+            // identified): the runtime creates the context if needed, then the
+            // address is looked up for it
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -197,6 +232,7 @@ extern "C" int qqa_round_eval_noalloc(int32_t kind, int32_t n, int64_t nnz, cons
                 return noalloc_fail(QQA_ECUDA, "cudaGetSymbolAddress of the static scratch failed");
             }
             g_scratch_addr[dev] = static_cast<NoAllocScratch *>(p);
+            g_scratch_ctx[dev] = current_context_id(&ctx_id) ? ctx_id : 0;
         }
         sc = g_scratch_addr[dev];
     }

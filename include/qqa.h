@@ -345,7 +345,9 @@ int qqa_run_step_debug(qqa_run *r, int32_t slot, void *stream, float *grad);
  * buffers when it is created and keeps them until qqa_server_destroy (class = S
  * rounded up to a power of two, >= 8; one run with a fixed launch shape and
  * its own stream per class). Each qqa_server_pump admits, advances every
- * class by `chunk_steps` annealing steps (the classes overlap on the device;
+ * class by `chunk_steps` annealing steps, or by up to 8 times that for a
+ * class with that much less work per step than the largest (the classes
+ * overlap on the device;
  * requests of a class share every step launch), evaluates, and retires the
  * requests that reached their own step count, freeing their slot and memory.
  * Requests therefore join and leave batches between chunks. A request's

@@ -6,9 +6,11 @@
 //      the HBM budget - every request is charged the exact device bytes its
 //      graph and state take - and a free slot of its replica class allow (graph
 //      upload, state allocation and initial draw happen here),
-//   2. advances every class run by one chunk of steps, each class on its own
-//      stream so the classes' work overlaps on the device; inside a class the
-//      requests share each step launch (one tile list),
+//   2. advances every class run by one or more chunks of steps (a class with
+//      less work per step runs more chunks in the time the largest class
+//      takes for one), each class on its own stream so the classes' work
+//      overlaps on the device; inside a class the requests share each step
+//      launch (one tile list),
 //   3. evaluates (projection rounding and exact costs) and retires the
 //      requests that reached their own step count, freeing slot and memory.
 // A request therefore joins or leaves a batch between chunks of steps, not
@@ -250,19 +252,39 @@ static void admit(qqa_server *s)
     }
 }
 
+// Work of one step of a class: the state elements of its running requests.
+static double class_work(const qqa_server *s, const ClassRun &c)
+{
+    double w = 0.0;
+    for (int64_t id : c.slot_req)
+        if (id >= 0) {
+            const Request *r = s->reqs.at(id).get();
+            w += (double)r->n * (double)c.S_class;
+        }
+    return w;
+}
+
 extern "C" int qqa_server_pump(qqa_server *s, int32_t *n_running, int32_t *n_queued, int32_t *n_finished)
 {
     if (!s) return QQA_EINVAL;
     admit(s);
-    // one chunk for every class with running requests, each on its own stream
+    // Every class with running requests advances on its own stream, so the
+    // classes run side by side; a pump lasts about as long as the class with
+    // the most work per step needs for one chunk, and a class with k times less
+    // work runs up to k chunks (at most 8) in that time, so small requests are
+    // not held to the pace of large ones.
+    double max_work = 0.0;
+    for (auto &kv : s->classes) max_work = std::max(max_work, class_work(s, kv.second));
     for (auto &kv : s->classes) {
         ClassRun &c = kv.second;
-        bool any = false;
-        for (int64_t id : c.slot_req) any |= id >= 0;
-        if (!any) continue;
-        int rc = qqa_run_steps(c.run, s->chunk, c.stream);
-        if (!rc) rc = qqa_run_eval(c.run, c.stream);
-        if (rc) return rc;
+        const double w = class_work(s, c);
+        if (w <= 0.0) continue;
+        const int32_t chunks = (int32_t)std::max(1.0, std::min(8.0, std::floor(max_work / w)));
+        for (int32_t k = 0; k < chunks; ++k) {   // a rounding after every chunk: the same history in any mix
+            int rc = qqa_run_steps(c.run, s->chunk, c.stream);
+            if (!rc) rc = qqa_run_eval(c.run, c.stream);
+            if (rc) return rc;
+        }
     }
     int32_t finished = 0;
     for (auto &kv : s->classes) {

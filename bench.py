@@ -697,7 +697,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ serving
-def serving_record(num: int, rate: float, seed: int, local: int):
+def serving_record(num: int, rate: float, seed: int, local: int, kernel: str = "pipe"):
     """Poisson trace of MIS / max-cut requests through the continuous-batching
     server, played twice: at the trace's own rate and at 0.7x the throughput
     the first play measured (its capacity). Latency is from arrival to
@@ -709,8 +709,11 @@ def serving_record(num: int, rate: float, seed: int, local: int):
     graphs = [W.graph_from_spec(spec) for _, spec, _ in trace]
     budget = 64 << 30
 
+    # the trace's graphs are sparse (average degree 10): every class takes the pipelined kernel
+    cfg = qqa.LaunchConfig(use_graphs=1, kernel=KERNEL_NAMES.index(kernel))
+
     def play(rate_scale: float):
-        srv = qqa.Server(budget, chunk_steps=50, slots_per_class=64, precision=W.BF16)
+        srv = qqa.Server(budget, chunk_steps=50, slots_per_class=64, precision=W.BF16, config=cfg)
         arrivals = [a / rate_scale for a, _, _ in trace]
         ids = {}
         live = set()
@@ -752,7 +755,7 @@ def serving_record(num: int, rate: float, seed: int, local: int):
     return {"metric": METRIC, "value": full["value"], "unit": METRIC,
             "workload": f"serving_poisson{int(rate)}_x{len(trace)}",
             "requests": "MIS/max-cut, ER avg degree 10, n log-uniform [1e3, 1e6], S in {32..256}, "
-                        "steps U[1000, 5000], BF16", "budget_bytes": budget, "chunk_steps": 50,
+                        "steps U[1000, 5000], BF16", "budget_bytes": budget, "chunk_steps": 50, "kernel": kernel,
             "at_rate": full, "at_0.7x_capacity": light, "clocks": clocks.summary(),
             "gpu_launches": full["gpu_launches"] + light["gpu_launches"]}
 
@@ -767,7 +770,8 @@ def run_serving(args):
     _build.build()
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
-    rec = serving_record(args.serve_requests, args.serve_rate, 9 + rank, local)
+    rec = serving_record(args.serve_requests, args.serve_rate, 9 + rank, local,
+                         "pipe" if args.kernel == "auto" else args.kernel)
     line = {"metric": METRIC, "value": rec["value"], "unit": METRIC, "n_gpus": world, "steps": 1, "warmup": 0,
             "ms_per_step": 1000 * rec["at_rate"]["wall_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-storage/f32-math", "data": "synthetic",

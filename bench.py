@@ -83,7 +83,8 @@ def read_peak():
 
 # device symbol of each step kernel variant (as ncu lists it)
 KERNEL_SYMBOL = {"direct": "qqa_step_kernel", "staged": "qqa_step_tiled_kernel", "stream": "qqa_step_stream_kernel",
-                 "dense": "qqa_step_dense_kernel", "pipe": "qqa_step_pipe_kernel", "scalar": "qqa_step_scalar_kernel"}
+                 "dense": "qqa_dense_gemm_kernel + qqa_dense_update_kernel", "pipe": "qqa_step_pipe_kernel",
+                 "scalar": "qqa_step_scalar_kernel"}
 KERNEL_NAMES = ["auto", "direct", "staged", "stream", "dense", "pipe", "scalar"]
 
 
@@ -102,7 +103,8 @@ def kernel_source_hash(kernel: str) -> str:
     """Hash of the sources the step kernel variant is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_02135_gb300", "csrc")
-    names = ["step_impl.cuh", "qqa_internal.cuh"] + (["step_dense.cu"] if kernel == "dense" else [])
+    names = ["step_impl.cuh", "qqa_internal.cuh"] + (["step_dense.cu", "step_dense_update.cu"] if kernel == "dense"
+                                                      else [])
     for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
@@ -110,8 +112,9 @@ def kernel_source_hash(kernel: str) -> str:
 
 
 def profiled_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    only if it was taken on the same kernel variant and its current source."""
+    """DRAM bytes of one step (the step kernel's launch; for the tensor-core
+    step its two kernels together) from the committed ncu summary, only if it
+    was taken on the same kernel variant and its current source."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}.md")
     if not os.path.exists(path):
         return None

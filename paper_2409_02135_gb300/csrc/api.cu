@@ -116,6 +116,10 @@ struct qqa_problem {
     // neighbours by the long-row kernel (device tables; none when nlong = 0)
     int32_t long_thresh = 0x7fffffff, nlong = 0, nseg = 0;
     int32_t *long_rows = nullptr, *seg_ptr = nullptr, *seg_row = nullptr;
+    // graphs with a wide spread of degrees (the largest row below the long-row
+    // threshold at least 4x the mean): each row's degree, 0 for long rows (host
+    // copy; empty otherwise). The pipelined kernel's tile list is ordered by it.
+    std::vector<uint16_t> short_deg;
     Alloc alloc;
 };
 
@@ -255,6 +259,21 @@ extern "C" int qqa_create_problem(int32_t kind, int32_t n, const int32_t *row_pt
     }
     p->nlong = (int32_t)lrows.size();
     p->nseg = (int32_t)lseg_row.size();
+    {
+        int32_t max_short = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t deg = row_ptr[i + 1] - row_ptr[i];
+            if (deg <= p->long_thresh) max_short = std::max(max_short, deg);
+        }
+        const int64_t mean_up = (p->nnz + n - 1) / std::max<int32_t>(n, 1);
+        if (n > 0 && (int64_t)max_short >= 4 * std::max<int64_t>(mean_up, 1)) {
+            p->short_deg.resize((size_t)n);
+            for (int32_t i = 0; i < n; ++i) {
+                const int32_t deg = row_ptr[i + 1] - row_ptr[i];
+                p->short_deg[(size_t)i] = deg > p->long_thresh ? 0 : (uint16_t)std::min(deg, 65535);
+            }
+        }
+    }
     p->row_ptr = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)(n + 1), st);
     p->col = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
     if (w) p->w = (int32_t *)p->alloc.get(sizeof(int32_t) * (size_t)std::max<int64_t>(p->nnz, 1), st);
@@ -645,10 +664,31 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
             if (!s.active || !r->h_descs[k].hub_active) continue;
             for (int32_t q = 0; q < s.prob->nseg; q += r->rows_per_tile) tiles.push_back(Tile{k, -(q + 1)});
         }
+    // Warps take the tiles round-robin, so on a graph whose row degrees spread
+    // widely (scale-free) a warp's share of the gather work varies with the
+    // tiles it happens to get, and the launch waits for the most loaded warp.
+    // For the pipelined kernel such a slot's tiles are listed by decreasing
+    // largest degree (stable, so rows of equal degree stay in order): each
+    // round of the walk then takes tiles of about equal cost, and the cheapest
+    // come last. The order does not change any result: rows are independent.
+    std::vector<std::pair<int32_t, int32_t>> keyed;   // (key, row0)
     for (int32_t k = 0; k < r->capacity; ++k) {
         const SlotHost &s = r->slots[k];
         if (!s.active) continue;
-        for (int32_t row0 = 0; row0 < s.n; row0 += r->rows_per_tile) tiles.push_back(Tile{k, row0});
+        const std::vector<uint16_t> &sd = s.prob->short_deg;
+        if (!fold || sd.empty()) {
+            for (int32_t row0 = 0; row0 < s.n; row0 += r->rows_per_tile) tiles.push_back(Tile{k, row0});
+            continue;
+        }
+        keyed.clear();
+        for (int32_t row0 = 0; row0 < s.n; row0 += r->rows_per_tile) {
+            int32_t key = 0;
+            for (int32_t i = row0; i < std::min(s.n, row0 + r->rows_per_tile); ++i) key = std::max<int32_t>(key, sd[(size_t)i]);
+            keyed.emplace_back(key, row0);
+        }
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const std::pair<int32_t, int32_t> &a, const std::pair<int32_t, int32_t> &b) { return a.first > b.first; });
+        for (const auto &kr : keyed) tiles.push_back(Tile{k, kr.second});
     }
     const int32_t nt = (int32_t)tiles.size();
     const bool seg_items = fold && !tiles.empty() && tiles.front().row0 < 0;

@@ -904,13 +904,12 @@ __device__ __forceinline__ void load_own_smem(const unsigned char *buf, int R, i
 }
 
 // SEGS: the tile list may hold segment work items of long rows (runs without
-// long rows take the variant without that path).
+// long rows take the variant without that path). The body of the pipelined
+// kernels below.
 template <typename T, int G, int VPL, bool SEGS>
-__global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__restrict__ descs,
-                                                            const Tile *__restrict__ tiles,
-                                                            const int32_t *__restrict__ num_tiles_p,
-                                                            RunStatus *__restrict__ status, int32_t r,
-                                                            int32_t buf_bytes)
+__device__ __forceinline__ void pipe_step(const InstDesc *__restrict__ descs, const Tile *__restrict__ tiles,
+                                          const int32_t *__restrict__ num_tiles_p, RunStatus *__restrict__ status,
+                                          int32_t r, int32_t buf_bytes)
 {
     constexpr int R = 32 / G;   // rows of a tile: one per lane group of the warp
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1159,6 +1158,29 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
         }
         __syncwarp();   // every lane is done with buffer b
     }
+}
+
+template <typename T, int G, int VPL, bool SEGS>
+__global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__restrict__ descs,
+                                                            const Tile *__restrict__ tiles,
+                                                            const int32_t *__restrict__ num_tiles_p,
+                                                            RunStatus *__restrict__ status, int32_t r,
+                                                            int32_t buf_bytes)
+{
+    pipe_step<T, G, VPL, SEGS>(descs, tiles, num_tiles_p, status, r, buf_bytes);
+}
+
+// With one vector per lane the kernel is held to 96 registers, so that five
+// blocks of 128 threads fit on an SM instead of four (a few bytes of spills;
+// measured faster on BA max-cut, where more warps hide more gather latency).
+template <typename T, int G, bool SEGS>
+__global__ void __maxnreg__(96) qqa_step_pipe_kernel_v1(const InstDesc *__restrict__ descs,
+                                                        const Tile *__restrict__ tiles,
+                                                        const int32_t *__restrict__ num_tiles_p,
+                                                        RunStatus *__restrict__ status, int32_t r,
+                                                        int32_t buf_bytes)
+{
+    pipe_step<T, G, 1, SEGS>(descs, tiles, num_tiles_p, status, r, buf_bytes);
 }
 
 // ---------------------------------------------------------------------------

@@ -344,6 +344,10 @@ struct SlotHost {
     int32_t best = -1, eval_step = -1, eval_count = 0;
 };
 
+// chains of a tensor-core run (see qqa_run::nchains): at most kMaxChains, kChains used
+static constexpr int kMaxChains = 4;
+static constexpr int kChains = 4;
+
 struct qqa_run {
     int32_t capacity = 0, S_max = 0, S_max_pad = 0, prec = 0, vec = 4;
     qqa_launch_config cfg{};
@@ -375,8 +379,20 @@ struct qqa_run {
     std::vector<InstDesc> h_descs;
     Tile *d_tiles = nullptr;
     int32_t tile_cap = 0;
-    int32_t *d_num_tiles = nullptr;  // [0] tiles, [1] streaming cache hints on (state larger than L2), [2] long-row items
-    int32_t tile_words[4] = {0, 0, 0, 0};
+    int32_t *d_num_tiles = nullptr;  // [0] tiles, [1] streaming cache hints on (state larger than L2), [2] long-row items,
+                                     // [3] update tiles; chained tensor-core runs: [4 + c] product tiles of chain c,
+                                     // [4 + kMaxChains + c] its update tiles
+    int32_t tile_words[4 + 2 * kMaxChains] = {};
+    // Tensor-core runs of several instances: the instances form up to
+    // kMaxChains chains of about equal row tiles, each launched on its own
+    // stream (forked from the caller's and joined back after the chunk). A
+    // chain's step waits only for its own previous step, so one chain's update
+    // runs beside another's product (the product kernel fills few SMs and
+    // waits on its loads) instead of after the product of every instance.
+    int32_t nchains = 1;
+    int32_t chain_t0[kMaxChains + 1] = {}, chain_u0[kMaxChains + 1] = {};   // first product / update tile of each chain
+    cudaStream_t chain_st[kMaxChains] = {};   // chains 1.. (chain 0 runs on the caller's stream)
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxChains] = {};
     int32_t num_tiles = 0;
     RunStatus *d_status = nullptr;
     float *d_scratch = nullptr;   // state import/export staging
@@ -777,6 +793,38 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     r->num_hub_items = nh;
     r->num_clique = nc;
     r->kernels_per_step = 1 + (r->upd_fn ? 1 : 0) + (nh ? 1 : 0) + (nc ? 1 : 0);
+    // chains: tensor-core runs of several instances with neither long rows nor
+    // clique column sums (both need every row of the step done); chain c takes
+    // whole instances, in slot order, until it holds its share of the row tiles
+    int32_t nch = 1, t0[kMaxChains + 1] = {}, u0[kMaxChains + 1] = {};
+    if (r->dense_N && !r->dynamic && nh == 0 && nc == 0 && r->chain_st[0]) {
+        int32_t active = 0;
+        for (int32_t k = 0; k < r->capacity; ++k) active += r->slots[k].active ? 1 : 0;
+        nch = std::max(1, std::min(kChains, active));
+        int32_t c = 0, ta = 0, ua = 0;
+        for (int32_t k = 0; k < r->capacity; ++k) {
+            const SlotHost &s = r->slots[k];
+            if (!s.active) continue;
+            if (c + 1 < nch && (int64_t)ta * nch >= (int64_t)(c + 1) * nt) {   // one new chain per instance at most
+                t0[++c] = ta;
+                u0[c] = ua;
+            }
+            ta += (s.n + r->rows_per_tile - 1) / r->rows_per_tile;
+            ua += (s.n + 31) / 32;
+        }
+        nch = c + 1;
+        t0[nch] = nt;
+        u0[nch] = nt2;
+    }
+    bool same = nch == r->nchains;
+    for (int32_t c = 0; c <= nch && same; ++c) same = t0[c] == r->chain_t0[c] && u0[c] == r->chain_u0[c];
+    if (!same) drop_graphs(r);
+    r->nchains = nch;
+    for (int32_t c = 0; c <= kMaxChains; ++c) {
+        r->chain_t0[c] = c <= nch ? t0[c] : 0;
+        r->chain_u0[c] = c <= nch ? u0[c] : 0;
+    }
+    if (nch > 1) r->kernels_per_step = 2 * nch;   // product and update of each chain
     // second word: the run's replica state (p^t, p^{t+1}, master, m, v) is larger
     // than most of L2, so streaming kernels mark it evict-first
     double state_bytes = 0.0;
@@ -790,7 +838,11 @@ static int rebuild_tiles(qqa_run *r, cudaStream_t st)
     r->tile_words[1] = state_bytes > 0.75 * (double)l2 ? 1 : 0;
     r->tile_words[2] = nh;
     r->tile_words[3] = nt2;
-    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, 4 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    for (int32_t c = 0; c < kMaxChains; ++c) {
+        r->tile_words[4 + c] = c < r->nchains ? r->chain_t0[c + 1] - r->chain_t0[c] : 0;
+        r->tile_words[4 + kMaxChains + c] = c < r->nchains ? r->chain_u0[c + 1] - r->chain_u0[c] : 0;
+    }
+    QQA_CK(cudaMemcpyAsync(r->d_num_tiles, r->tile_words, sizeof r->tile_words, cudaMemcpyHostToDevice, st));
     QQA_CK(cudaStreamSynchronize(st));
     r->num_tiles = nt;
     return QQA_OK;
@@ -832,7 +884,7 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     r->h_descs.assign(capacity, InstDesc{});
     r->slots.resize(capacity);
     r->d_descs = (InstDesc *)r->alloc.get(sizeof(InstDesc) * (size_t)capacity, st);
-    r->d_num_tiles = (int32_t *)r->alloc.get(4 * sizeof(int32_t), st);
+    r->d_num_tiles = (int32_t *)r->alloc.get(sizeof r->tile_words, st);
     r->d_status = (RunStatus *)r->alloc.get(sizeof(RunStatus), st);
     if (!r->d_descs || !r->d_num_tiles || !r->d_status) {
         qqa_run_destroy(r);
@@ -840,9 +892,16 @@ static int run_create_hinted(int32_t capacity, int32_t S_max, int32_t precision,
     }
     cudaError_t e = cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)capacity,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, 4 * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_num_tiles, 0, sizeof r->tile_words, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_status, 0, sizeof(RunStatus), st);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && r->dense_N) {   // the chains' streams and events
+        e = cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming);
+        for (int c = 0; c < kChains - 1 && e == cudaSuccess; ++c) {
+            e = cudaStreamCreateWithFlags(&r->chain_st[c], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_join[c], cudaEventDisableTiming);
+        }
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         qqa_run_destroy(r);
@@ -1337,6 +1396,11 @@ extern "C" void qqa_run_destroy(qqa_run *r)
     r->alloc.put(r->d_status, 0);
     r->alloc.put(r->d_scratch, 0);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
+    if (r->ev_fork) cudaEventDestroy(r->ev_fork);
+    for (int c = 0; c < kMaxChains; ++c) {
+        if (r->chain_st[c]) cudaStreamDestroy(r->chain_st[c]);
+        if (r->ev_join[c]) cudaEventDestroy(r->ev_join[c]);
+    }
     delete r;
 }
 
@@ -1348,8 +1412,37 @@ extern "C" int qqa_run_config(const qqa_run *r, qqa_launch_config *out)
 }
 
 // ------------------------------------------------------------------- steps
+// The steps of a chunk for a chained tensor-core run: chain 0 on st, chain c
+// on the run's stream c - 1 (forked from st and joined back at the end). Each
+// chain's steps depend only on its own previous step.
+static int launch_chains(qqa_run *r, int32_t chunk, cudaStream_t st)
+{
+    const int32_t nch = r->nchains;
+    launch_prepare(r->d_descs, r->capacity, chunk, st);
+    QQA_CK(cudaEventRecord(r->ev_fork, st));
+    for (int32_t c = 1; c < nch; ++c) QQA_CK(cudaStreamWaitEvent(r->chain_st[c - 1], r->ev_fork, 0));
+    for (int32_t i = 0; i < chunk; ++i)
+        for (int32_t c = 0; c < nch; ++c) {
+            cudaStream_t s = c == 0 ? st : r->chain_st[c - 1];
+            const int32_t nt = r->chain_t0[c + 1] - r->chain_t0[c], nu = r->chain_u0[c + 1] - r->chain_u0[c];
+            r->step_fn<<<std::max(1, std::min(r->max_grid, nt)), r->cfg.block_threads, r->smem, s>>>(
+                r->d_descs, r->d_tiles + r->chain_t0[c], r->d_num_tiles + 4 + c, r->d_status, i);
+            r->upd_fn<<<std::max(1, std::min(r->upd_max_grid, nu)), r->upd_block, r->upd_smem, s>>>(
+                r->d_descs, r->d_tiles2 + r->chain_u0[c], r->d_num_tiles + 4 + kMaxChains + c, r->d_status, i,
+                r->upd_ld);
+        }
+    for (int32_t c = 1; c < nch; ++c) {
+        QQA_CK(cudaEventRecord(r->ev_join[c - 1], r->chain_st[c - 1]));
+        QQA_CK(cudaStreamWaitEvent(st, r->ev_join[c - 1], 0));
+    }
+    launch_advance(r->d_descs, r->capacity, chunk, st);
+    QQA_CK_LAUNCH("step");
+    return QQA_OK;
+}
+
 static int launch_step_chunk(qqa_run *r, int32_t chunk, int32_t grid, cudaStream_t st)
 {
+    if (r->nchains > 1) return launch_chains(r, chunk, st);
     launch_prepare(r->d_descs, r->capacity, chunk, st);
     for (int32_t i = 0; i < chunk; ++i) {
         if (r->tiled_fn)

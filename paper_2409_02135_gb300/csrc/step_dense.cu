@@ -1,6 +1,6 @@
-// step_dense.cu -- the fused PQQA step on the 5th-generation tensor cores, for
-// dense graphs (FP32 runs, and BF16 runs, whose planes come from the FP32
-// master).
+// step_dense.cu -- the product of the PQQA step on the 5th-generation tensor
+// cores, for dense graphs (FP32 runs, and BF16 runs, whose planes come from
+// the FP32 master).
 //
 // The sparse product of the step, Y[i][s] = sum_j A_ij p^t[j][s] (Eqs. 22, 24,
 // 26), is a dense contraction when the graph is dense (ER with p = 0.15 has
@@ -12,17 +12,15 @@
 //     significant bits, and D = A.hi + A.lo is accumulated in FP32 in tensor
 //     memory (every product is exact), so Y matches the FP32 gather to the
 //     rounding of an FP32 sum;
-//   - one CTA owns 128 rows of one instance: a control thread streams 64-wide
-//     K chunks of A and of both planes into shared memory with TMA (128-byte
-//     swizzle, 3 stages - 2 at N = 256 - mbarrier completion, bounded waits) and issues
-//     tcgen05.mma (M = 128, N = dense_N, K = 16) into a TMEM accumulator;
-//   - 16 epilogue warps read the accumulator with tcgen05.ld (TMEM lane =
-//     row, column = replica), form the row statistics over the S replicas
-//     through shared memory, and apply the gradient, AdamW, noise and clamp
-//     exactly as the other step kernels do. They write p^{t+1} (FP32; in BF16
-//     runs the BF16 state and the FP32 master) and, from the FP32 value, the
-//     two transposed fp16 planes for the next step's GEMM (one row per lane,
-//     so the plane writes are coalesced).
+//   - one CTA owns 128 rows of one instance: one thread streams 64-wide K
+//     chunks of A and of both planes into shared memory with TMA (128-byte
+//     swizzle, 4 stages - 2 at N = 256 - mbarrier completion, bounded waits),
+//     another issues tcgen05.mma (M = 128, N = dense_N, K = 16) into a TMEM
+//     accumulator as the chunks land, and four warps read the accumulator
+//     with tcgen05.ld and store Y [n][S_pad] (FP32).
+// The rest of the step (gradient, statistics, AdamW, noise, clamp, and the
+// next step's planes) is the update kernel of step_dense_update.cu, which
+// runs on every SM over 32-row tiles.
 #include <cuda.h>
 #include <cuda_fp16.h>
 

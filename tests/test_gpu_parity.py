@@ -366,6 +366,31 @@ def test_dense_step_batch_of_uneven_instances_and_quality():
         assert f and o == a["obj"][a["best"]]
 
 
+@pytest.mark.parametrize("use_graphs", [1, 0], ids=["graphs", "launches"])
+@pytest.mark.parametrize("prec", [FP32, BF16])
+def test_dense_chained_batch_equals_each_instance_alone(prec, use_graphs):
+    """A tensor-core run of several instances launches them as up to four
+    chains of whole instances, each on its own stream, whose steps depend only
+    on the chain's own previous step: every instance (uneven n, some finishing
+    early) ends bit-identical to itself run alone, with and without CUDA
+    graphs, and the step launches a product and an update per chain."""
+    gs = [G.erdos_renyi(n, 0.15, 900 + k) for k, n in enumerate((700, 300, 777, 540, 800, 129))]
+    ps = [Params(S=128, steps=s, lr=1.0, seed=k, precision=prec) for k, s in enumerate((60, 25, 60, 40, 60, 60))]
+    cfg = qqa.LaunchConfig(kernel=qqa.KERNEL_DENSE, use_graphs=use_graphs)
+    batch = make_run(MIS, gs, ps, config=cfg)
+    n0 = qqa.launch_count()
+    batch.steps(50)
+    per_step = (qqa.launch_count() - n0 - 2) / 50   # prepare and advance once per chunk
+    assert per_step in (4, 6, 8), per_step   # a product and an update per chain, 2 to 4 chains
+    batch.steps(10)
+    assert [batch.slot_step(k) for k in range(len(gs))] == [60, 25, 60, 40, 60, 60]
+    for k in range(len(gs)):
+        alone = make_run(MIS, gs[k], ps[k], config=cfg)
+        alone.steps(60)
+        for a, b in zip(alone.get_state(0)[:3], batch.get_state(k)[:3]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_staged_kernel_single_step_parity_dense_graph():
     g = G.erdos_renyi(750, 0.15, 1000)
     p = Params(S=128, steps=3000, alpha_comm=0.3, seed=0)

@@ -1116,8 +1116,10 @@ __device__ __forceinline__ void pipe_step(const InstDesc *__restrict__ descs, co
         // the next tile's first neighbour rows (one per lane of the group, up to
         // G of them) are pulled from L2 into L1 while this tile is updated, so
         // its gather finds them there; its row bounds and first indices were
-        // requested before this tile's gather
-        if (has_next && ix_cur.k0 + gl < ix_cur.k1) {
+        // requested before this tile's gather. With one vector per lane (one
+        // row per warp, five blocks per SM) the L1 is shared by more warps and
+        // the prefetch measured slower, so that variant leaves it out.
+        if (VPL != 1 && has_next && ix_cur.k0 + gl < ix_cur.k1) {
             const void *xn = xcur;
             int spn = c.S_pad;
             bool live = true;

@@ -102,9 +102,15 @@ typedef struct qqa_params {
  *                 product A.p runs on the tensor cores - tcgen05.mma on an
  *                 fp16 adjacency and two fp16 planes of p (formed from the
  *                 FP32 state, the master in BF16 runs), FP32 accumulation
- *                 in tensor memory - fused with the rest of the step; needs
- *                 an n_pad^2 fp16 adjacency per instance, n_pad = n rounded
- *                 up to 128; edge weights must be exact in fp16, |w| <= 2048)
+ *                 in tensor memory - followed by an update kernel for the
+ *                 rest of the step; needs an n_pad^2 fp16 adjacency per
+ *                 instance, n_pad = n rounded up to 128; edge weights must be
+ *                 exact in fp16, |w| <= 2048. A run of several instances
+ *                 without long rows or max-clique instances steps them as up
+ *                 to four chains of whole instances, each on a stream the run
+ *                 owns, forked from the caller's stream and joined back to it
+ *                 before qqa_run_steps returns its work to that stream; the
+ *                 results equal those of each instance run alone)
  *                 or QQA_KERNEL_PIPE (sparse graphs: every warp bulk-copies
  *                 the next rows it owns of p, m and v into its own shared-
  *                 memory double buffer while it updates the current ones)
@@ -114,7 +120,8 @@ typedef struct qqa_params {
  *                 without padding, and kernel_param lanes (4, 8, 16, 32) share
  *                 one node's neighbour list in the sparse product
  *   Rows whose degree exceeds max(64, 8 x the graph's mean degree) are updated
- *   by a separate long-row kernel launched with the gather kernels: their
+ *   by a separate long-row kernel launched with the gather kernels (the
+ *   pipelined kernel takes their segments as work items of its own): their
  *   neighbour lists are summed in segments of 32 CSR entries by separate lane
  *   groups, then combined in segment order (FP32), so a hub of a scale-free
  *   graph does not hold up the step.

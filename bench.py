@@ -384,12 +384,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ sub-records
-def workload_record(name: str, local: int, stream, alloc, flush, timed: int = 3, warmup: int = 2):
+def workload_record(name: str, local: int, stream, alloc, flush, timed: int = 3, warmup: int = 2,
+                    cpu_seconds: float = 0.0):
     """One more workload measured the way the headline is (device-timed whole
     anneals after an autotuned launch shape, L2 flushed between anneals,
     clocks sampled while timing): replica-steps/s, the step kernel's roofline,
-    the best objective and the time to the oracle's quality. Used for the
-    graded HBM-bound max-cut configurations beside the default workload."""
+    the best objective and the time to the oracle's quality, and (cpu_seconds
+    > 0) the FP64 oracle timed on a bounded sample of the same workload. Used
+    for the graded HBM-bound max-cut configurations beside the default
+    workload."""
     import torch
     import paper_2409_02135_gb300 as qqa
     wl = build_workload(name, 0)
@@ -450,9 +453,15 @@ def workload_record(name: str, local: int, stream, alloc, flush, timed: int = 3,
            "best_objective": int(res["obj"][res["best"]]) if res["best"] >= 0 else None,
            "time_to_oracle_quality": time_to_quality(name, run, len(probs), se[-1][0], ev[-1], R),
            "l2": "flushed between timed anneals (512 MB write)"}
+    rec["replica_node_updates_per_s"] = sum(i.graph.n * i.params.S * i.params.steps
+                                            for i in wl.instances) / (statistics.mean(ms) / 1000.0)
     run.close()
     for pb in probs:
         pb.close()
+    if cpu_seconds > 0:
+        v, dt, cores, desc = oracle_sample(wl, oracle_steps_for(wl, cpu_seconds))
+        rec["cpu_baseline"] = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc,
+                               "seconds": dt}
     return rec
 
 
@@ -695,7 +704,8 @@ def run_ours(args):
     # the graded HBM-bound configurations (max-cut n = 1e5, S = 256, BF16) beside the default workload
     if args.workload == "mis_er700_800" and world == 1 and not args.no_subrecords:
         for name in ("maxcut_regular3", "maxcut_ba4"):
-            line[name] = workload_record(name, local, stream, alloc, flush)
+            line[name] = workload_record(name, local, stream, alloc, flush,
+                                         cpu_seconds=0.0 if args.no_cpu_baseline else args.cpu_seconds / 2)
         # the fused sparse (CSR gather, no tensor cores) step on the HBM-bound
         # configurations, the kernel the 70% roofline target is about; the
         # headline above is the tensor-core step on the L2-resident default

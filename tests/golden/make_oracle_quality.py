@@ -12,6 +12,13 @@ bench.py's time-to-oracle-quality figure.
 Each set names a workload recipe, the instances it takes and the number of
 oracle seeds (run seed 1000 + k for seed k). The output is rewritten after
 every seed, so an interrupted run keeps what it finished and a rerun resumes.
+
+Long sets can run their seeds in parallel processes: `--seed k` computes run
+k of a single-instance set alone into oracle_quality_<set>.seed<k>.json, and
+the main mode takes such a file in place of computing that run (and removes
+it once the run is in the set's file).
+
+    python tests/golden/make_oracle_quality.py maxcut_regular3_n100000 --seed 3
 """
 import json
 import os
@@ -55,14 +62,39 @@ SETS = {
 }
 
 
+def _one_run(inst, seed):
+    """Run `seed` of an instance: best feasible objective, feasible count, lowest energy."""
+    r = oracle.anneal(inst.kind, inst.graph, inst.params.with_(seed=1000 + seed))
+    e = r.eval
+    return (int(e.obj[e.best]) if e.best >= 0 else None, int(np.count_nonzero(e.feasible)),
+            float(np.min(e.energy)))
+
+
 def main():
-    name = sys.argv[1] if len(sys.argv) > 1 else "mis_er700_800"
+    args = [a for a in sys.argv[1:]]
+    only = None
+    if "--seed" in args:
+        k = args.index("--seed")
+        only = int(args[k + 1])
+        del args[k:k + 2]
+    name = args[0] if args else "mis_er700_800"
     factory, seeds, take = SETS[name]
-    if len(sys.argv) > 2:
-        seeds = int(sys.argv[2])
+    if len(args) > 1:
+        seeds = int(args[1])
     wl = factory()
     insts = wl.instances if take is None else wl.instances[:take]
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"oracle_quality_{name}.json")
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, f"oracle_quality_{name}.json")
+    part = lambda k: os.path.join(here, f"oracle_quality_{name}.seed{k}.json")  # noqa: E731
+    if only is not None:   # one run of a single-instance set, for a parallel process
+        assert len(insts) == 1, "--seed is for single-instance sets"
+        best, feas, emin = _one_run(insts[0], only)
+        with open(part(only) + ".tmp", "w") as f:
+            json.dump({"set": name, "name": insts[0].name, "seed": only, "oracle_best": best,
+                       "oracle_feasible": feas, "oracle_min_energy": emin}, f, indent=1)
+        os.replace(part(only) + ".tmp", part(only))
+        print(name, insts[0].name, only, best, "(part file)", flush=True)
+        return
     done = {}
     if os.path.exists(path):
         for rec in json.load(open(path)).get("instances", []):
@@ -87,15 +119,24 @@ def main():
         out["instances"].append(rec)
         for seed in range(len(rec["oracle_best"]), seeds):
             t0 = time.time()
-            r = oracle.anneal(inst.kind, inst.graph, p0.with_(seed=1000 + seed))
-            e = r.eval
-            rec["oracle_best"].append(int(e.obj[e.best]) if e.best >= 0 else None)
-            rec["oracle_feasible"].append(int(np.count_nonzero(e.feasible)))
-            rec["oracle_min_energy"].append(float(np.min(e.energy)))
+            pf = part(seed)
+            if len(insts) == 1 and os.path.exists(pf):   # computed by a parallel process
+                with open(pf) as f:
+                    got = json.load(f)
+                assert got["set"] == name and got["seed"] == seed
+                best, feas, emin = got["oracle_best"], got["oracle_feasible"], got["oracle_min_energy"]
+            else:
+                best, feas, emin = _one_run(inst, seed)
+                pf = None
+            rec["oracle_best"].append(best)
+            rec["oracle_feasible"].append(feas)
+            rec["oracle_min_energy"].append(emin)
             ok = [b for b in rec["oracle_best"] if b is not None]
             rec["oracle_mean_best"] = float(np.mean(ok)) if ok else None
             rec["oracle_mean_min_energy"] = float(np.mean(rec["oracle_min_energy"]))
             write()
+            if pf:
+                os.remove(pf)
             print(name, inst.name, seed, rec["oracle_best"][-1], f"{time.time() - t0:.1f}s", flush=True)
         ok = [b for b in rec["oracle_best"] if b is not None]
         rec["oracle_mean_best"] = float(np.mean(ok)) if ok else None

@@ -949,7 +949,15 @@ __device__ __forceinline__ void pipe_step(const InstDesc *__restrict__ descs, co
     const void *xcur = nullptr;
     uint64_t my_hint = 0;
     int ctx_slot = -1;
-    StepCtx c{};
+    // With one vector per lane the step scalars of the current instance live
+    // in shared memory (one copy per warp) rather than in registers, which
+    // lets the register-capped variant run without spills (BA(4) max-cut
+    // 157.4 -> 149.3 us at 96 registers); with more vectors per lane they stay
+    // in registers (3-regular max-cut measured 0.5% slower from shared memory).
+    constexpr bool kCtxShared = VPL == 1;
+    __shared__ StepCtx ctx_sm[kCtxShared ? 8 : 1];   // at most 8 warps per block
+    StepCtx ctx_reg{};
+    StepCtx &c = kCtxShared ? ctx_sm[warp] : ctx_reg;
     auto issue = [&](const Tile &tl, int b) -> bool {
         if (SEGS && tl.row0 < 0) return false;   // segments of long rows: no slabs
         int S_pad, n;
@@ -1043,7 +1051,12 @@ __device__ __forceinline__ void pipe_step(const InstDesc *__restrict__ descs, co
         if (tl.slot != ctx_slot) {
             const int t = d->t + r;
             if (t >= d->K) continue;   // finished instance: no copy was issued, nothing is read
-            c = make_ctx(d, t, r);
+            if (kCtxShared) {
+                if (lane == 0) c = make_ctx(d, t, r);
+                __syncwarp();   // the warp's lanes read it below
+            } else {
+                c = make_ctx(d, t, r);
+            }
             ctx_slot = tl.slot;
             xcur = d->X[t & 1];
             if (lane == 0) my_slab = reinterpret_cast<const unsigned char *>(d->master ? d->master : reinterpret_cast<const float *>(d->X[t & 1]));
@@ -1172,11 +1185,13 @@ __global__ void __launch_bounds__(256) qqa_step_pipe_kernel(const InstDesc *__re
     pipe_step<T, G, VPL, SEGS>(descs, tiles, num_tiles_p, status, r, buf_bytes);
 }
 
-// With one vector per lane the kernel is held to 96 registers, so that five
-// blocks of 128 threads fit on an SM instead of four (a few bytes of spills;
-// measured faster on BA max-cut, where more warps hide more gather latency).
+// With one vector per lane (and the step scalars in shared memory) the kernel
+// is held to 80 registers without spills, so that six blocks of 128 threads
+// fit on an SM instead of four: more warps hide more of the dependent gather
+// latency (BA(4) max-cut n = 1e5: 157.4 us at 127 registers, 149.3 at 96,
+// 138.4 at 80; 72 registers spill and measured 139.5).
 template <typename T, int G, bool SEGS>
-__global__ void __maxnreg__(96) qqa_step_pipe_kernel_v1(const InstDesc *__restrict__ descs,
+__global__ void __maxnreg__(80) qqa_step_pipe_kernel_v1(const InstDesc *__restrict__ descs,
                                                         const Tile *__restrict__ tiles,
                                                         const int32_t *__restrict__ num_tiles_p,
                                                         RunStatus *__restrict__ status, int32_t r,

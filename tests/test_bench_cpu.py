@@ -72,3 +72,14 @@ def test_profile_summaries_carry_their_variant_hash_and_traffic():
         assert re.search(r"kernel_source_sha256_16:\s*[0-9a-f]{16}\b", text), f
         traffic = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
         assert traffic and float(traffic.group(1)) > 0, f
+
+
+def test_quality_ratio_against_the_stored_oracle_means():
+    """The bench line's quality_vs_oracle divides each instance's best by the
+    oracle's stored mean (16 runs where stored, else 4) and leaves instances
+    without a target or a feasible replica as None."""
+    q = bench.quality_vs_oracle("maxcut_regular3", [136310.75])
+    assert q["oracle_runs"] == [4] and abs(q["ratio_per_instance"][0] - 1.0) < 1e-12
+    q = bench.quality_vs_oracle("mis_er700_800", [None] + [45] * 15)
+    assert q["ratio_per_instance"][0] is None and q["oracle_runs"][0] == 16 and len(q["oracle_runs"]) == 16
+    assert bench.quality_vs_oracle("no_such_workload", [1]) is None

@@ -1292,9 +1292,11 @@ extern "C" int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stre
         r->h_descs[k].t = r->slots[k].t;
         r->h_descs[k].last_eval_t = r->slots[k].last_eval_t;
     }
+    // (a copy from pageable host memory is staged before the call returns, so
+    // the table may change afterwards; the host does not wait for the device
+    // here, and a caller can queue several anneals ahead)
     QQA_CK(cudaMemcpyAsync(r->d_descs, r->h_descs.data(), sizeof(InstDesc) * (size_t)r->capacity,
                            cudaMemcpyHostToDevice, st));
-    QQA_CK(cudaStreamSynchronize(st));
     for (int32_t k = 0; k < r->capacity; ++k) {
         if ((slot >= 0 && k != slot) || !r->slots[k].active) continue;
         const SlotHost &s = r->slots[k];

@@ -202,7 +202,8 @@ int qqa_run_add(qqa_run *r, const qqa_problem *prob, const qqa_params *prm, void
 /*
  * Restart one slot (slot >= 0) or every active slot (slot = -1) from a fresh
  * initial state drawn with `seed` (the same draw as qqa_run_add) (step t = 0, m = v = 0, history cleared),
- * keeping its allocations. Asynchronous except for a small descriptor upload.
+ * keeping its allocations. Stream-ordered; the host does not wait for the
+ * device (the descriptor table is copied from host memory before it returns).
  */
 int qqa_run_reset(qqa_run *r, int32_t slot, uint64_t seed, void *stream);
 /* Release one instance's state; its slot becomes free. Stream-ordered. */
